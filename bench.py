@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Benchmark of the FLASH Viterbi decoding hot path on one GB300.
+
+Workload (default): 1024 sequences, K = 256 dense FP32 log-transitions
+(Dirichlet(1) rows), per-step emission scores log_softmax(N(0,1)), T uniform
+in [500, 4000]; one batched, uneven-length decode per step.  The metric is
+state-steps/s = sum_b T_b * K per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode vanilla|flash]
+    python bench.py --impl reference      # the CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank decodes its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "state-steps/s (sum T*K) vs plain GPU Viterbi, bit-exact paths; serving p99 latency"
+UNIT = "state-steps/s"
+WORKLOAD = "batched-uneven: 1024 seqs, K=256 dense FP32, T~U[500,4000], E=log_softmax(N(0,1))"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tops(sm_mhz):
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x clock, one op per lane
+    per cycle (a cell costs 2 ops: FADD + FMNMX)."""
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
+
+
+def make_workload(args, rank, device):
+    import torch
+
+    import paper_2510_19301_gb300 as fv
+    import workloads as W
+    K = 256
+    log_pi, logA = W.config2_model(seed=2)
+    lengths = W.config2_lengths(seed=2 + 7919 * rank, n_seq=args.n_seq)
+    E = W.gaussian_emissions_packed_device(int(lengths.sum()), K, seed=2 + 7919 * rank, device=device)
+    m = fv.Model(log_pi, logA, device=device)
+    return dict(K=K, log_pi=log_pi, logA=logA, lengths=lengths, E=E, model=m)
+
+
+def cpu_baseline(wl, seconds_target=20.0):
+    """The oracle as it stands, on the host cores, one sequence per thread,
+    over a bounded sample of the same batch (first sequences in batch order)."""
+    import oracle
+    oracle.build()
+    K = wl["K"]
+    lengths = wl["lengths"]
+    hmm = oracle.HMM(wl["log_pi"], wl["logA"])
+    cores = os.cpu_count() or 1
+    n = min(len(lengths), 8 * cores)
+    e_off = np.concatenate([[0], np.cumsum(lengths.astype(np.int64) * K)])
+    Eflat = wl["E"].view(-1)
+    jobs = [Eflat[e_off[i]:e_off[i + 1]].view(-1, K).cpu().numpy() for i in range(n)]
+    t0 = time.perf_counter()
+    oracle.map_sequences(lambda e: oracle.viterbi(hmm, e), jobs, threads=cores)
+    dt = time.perf_counter() - t0
+    steps = int(lengths[:n].astype(np.int64).sum()) * K
+    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of {len(lengths)} sequences ({steps} state-steps), exact vanilla oracle, "
+                      f"{cores} threads, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    oracle.build()
+    K = 256
+    log_pi, logA = W.config2_model(seed=2)
+    lengths = W.config2_lengths(seed=2, n_seq=args.n_seq)
+    hmm = oracle.HMM(log_pi, logA)
+    cores = os.cpu_count() or 1
+    n = cores  # one sequence per core per step: a bounded sample of the batch
+    rng = np.random.default_rng(123)
+    times, total = [], 0
+    for it in range(args.warmup + args.steps):
+        idx = [(it * n + k) % len(lengths) for k in range(n)]
+        jobs = [W.gaussian_emissions(int(lengths[i]), K, rng) for i in idx]
+        t0 = time.perf_counter()
+        oracle.map_sequences(lambda e: oracle.viterbi(hmm, e), jobs, threads=cores)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            total += int(sum(int(lengths[i]) for i in idx)) * K
+    T = sum(times)
+    v = total / T
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "mode": "vanilla", "sample_per_step": f"{n} sequences"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n} sequences of the workload per step (one per core), exact vanilla oracle"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2510_19301_gb300 as fv
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    wl = make_workload(args, rank, device)
+    K = wl["K"]
+    lengths = wl["lengths"]
+    m = wl["model"]
+    batch = fv.Batch(lengths, E=wl["E"].view(-1), models=[m], device=device)
+    dec = fv.Decoder([m], batch, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)
+    lib = fv._lib.load()
+    state_steps = int(lengths.astype(np.int64).sum()) * K
+    cells = int((lengths.astype(np.int64) - 1).sum()) * K * K
+
+    # correctness gate of the timed configuration: device status must be OK
+    dec(check=True)
+    for _ in range(args.warmup):
+        dec.launch()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    lib.fv_timing_enable(1)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        dec.launch()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    import ctypes
+    tot = ctypes.c_float(0)
+    npairs = ctypes.c_int32(0)
+    lib.fv_timing_read(ctypes.byref(tot), ctypes.byref(npairs))
+    lib.fv_timing_enable(0)
+    fwd_ms = tot.value / max(npairs.value, 1)
+    status = dec.device_status()
+    assert status == 0, f"device status {status}"
+
+    t_max = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = world * state_steps / (ms_max / 1e3)
+
+    # end to end through the public API: pinned host E -> device, decode,
+    # paths + scores -> pinned host, every step
+    E_host = torch.empty(wl["E"].numel(), dtype=torch.float32, pin_memory=True)
+    E_host.copy_(wl["E"].view(-1))
+    P_host = torch.empty(dec.paths.numel(), dtype=torch.int32, pin_memory=True)
+    S_host = torch.empty(dec.scores.numel(), dtype=torch.float32, pin_memory=True)
+    Edev = batch.E
+    e2e_steps = max(3, min(args.steps, 20))
+    for it in range(1 + e2e_steps):
+        if it == 1:
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(st)
+        Edev.copy_(E_host, non_blocking=True)
+        dec.launch()
+        P_host.copy_(dec.paths, non_blocking=True)
+        S_host.copy_(dec.scores, non_blocking=True)
+    f1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    h2d = E_host.numel() * 4
+    d2h = P_host.numel() * 4 + S_host.numel() * 4
+
+    pk, pk_kind = peaks()
+    sm_mhz = clocks["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
+    peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
+    achieved = 2.0 * cells / (fwd_ms / 1e3) / 1e12
+    launches = args.steps * 4
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "mode": args.mode, "P": args.P, "B": args.B,
+                      "n_seq": int(len(lengths)), "sum_T": int(lengths.sum()), "K": K,
+                      "l2": "inputs larger than L2 (E is %.2f GB per step)" % (wl["E"].numel() * 4 / 1e9)},
+           "clocks": clocks,
+           "gpu_launches": launches,
+           "roofline": {"bound": "alu", "kernel": "dense_fwd_kernel", "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (max clock)" % pk.get(
+                            "sm_max_mhz", 2070.0),
+                        "ops_per_cell": 2, "cells_per_launch": cells, "kernel_ms": fwd_ms},
+           "e2e": {"value": world * state_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="vanilla", choices=["vanilla", "flash", "beam"])
+    ap.add_argument("--P", type=int, default=16)
+    ap.add_argument("--B", type=int, default=0)
+    ap.add_argument("--budget", type=int, default=0)
+    ap.add_argument("--n-seq", dest="n_seq", type=int, default=1024)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * fv.h -- C ABI of libfv, a GB300 (sm_103a) implementation of the decoding
+ * hot path of FLASH Viterbi (Deng et al., arXiv 2510.19301).
+ *
+ * Operations (paper references are to that article):
+ *   - exact Viterbi decoding, Sec. III-A: delta_t(j) = max_i[delta_{t-1}(i)
+ *     A_ij] B_j(x_t) with argmax backpointers psi_t(j), evaluated in the log
+ *     domain (Sec. III-A, last paragraph);
+ *   - FLASH Viterbi, Sec. V-A/V-B: Alg. 1 (non-recursive divide and conquer
+ *     with the P-way first split of Sec. V-A.3) running Alg. 2 (subtask
+ *     decoding with MidState) under the pruned initialisation of Sec. V-B.2;
+ *   - dynamic beam search and FLASH-BS, Sec. V-C;
+ *   - a path-count backward (not in the paper).
+ *
+ * Numerics: every score is IEEE binary32, round-to-nearest-even, in this
+ * order: delta_0[j] = logpi[j] + E_0[j];
+ *   delta_t[j] = (max_i (delta_{t-1}[i] + logA[i][j])) + E_t[j],
+ * every argmax takes the LOWEST index, and the value kept is the winning
+ * candidate itself.  FLASH uses the retained offset of Def. 3,
+ *   delta_m[j] = ((delta_{m-1}[q_{m-1}] + logA[q_{m-1}][j]) + E_m[j]),
+ * so its paths and scores are bit-identical to the exact decoder.
+ *
+ * Memory: all array pointers are DEVICE pointers owned by the caller unless
+ * the field name ends in _host.  The library never allocates device memory:
+ * every scratch byte lives in the caller's workspace (size from
+ * fv_workspace_size).  No pointer is retained after a call returns.  Work is
+ * enqueued on the given stream; calls return before the GPU finishes.
+ *
+ * Errors: argument errors are returned at once and nothing is enqueued.
+ * Errors found on the device (bad lengths or model indices, a workspace too
+ * small for the lengths actually present, a wait that ran out, an
+ * infeasible beam) are recorded in a status word inside the workspace; read
+ * it with fv_last_device_status after the stream is synchronised.  Nothing
+ * traps, aborts or prints.
+ */
+#ifndef FV_H
+#define FV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fv_stream_t; /* same handle as cudaStream_t */
+
+typedef enum {
+  FV_OK = 0,
+  FV_EINVAL = 1,        /* bad argument                                   */
+  FV_ENOMEM = 2,        /* workspace too small                             */
+  FV_ECUDA = 3,         /* a CUDA runtime call failed                      */
+  FV_ETIMEOUT = 4,      /* a bounded device wait ran out                   */
+  FV_EUNSUPPORTED = 5,  /* valid request this build does not implement     */
+  FV_EINFEASIBLE = 6    /* no finite path (beam emptied / unreachable q_n) */
+} fv_status;
+
+typedef enum {
+  FV_VANILLA = 0, /* full T x K uint16 backpointer table + backtrack (Sec. III-A) */
+  FV_FLASH = 1,   /* non-recursive D&C with MidState (Alg. 1, Alg. 2)            */
+  FV_BEAM = 2     /* dynamic beam (Sec. V-C); P >= 1 makes it FLASH-BS          */
+} fv_mode;
+
+typedef enum { FV_TRANS_DENSE = 0, FV_TRANS_CSR = 1 } fv_trans_kind;
+typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
+
+/* fv_params.flags */
+#define FV_COMPLETE_PRUNING 0x1u /* offset-0 re-initialisation of Sec. V-B.2     */
+#define FV_NO_SORT 0x2u          /* keep batch order (skip longest-first order)  */
+
+/* One HMM, lambda = (pi, A, B) of Sec. III. K <= 65536 (backpointers are
+ * uint16).  Dense transitions: logA[i*K + j] = log A_ij, row = source state.
+ * CSR transitions: out-edges of state i are col[row_ptr[i] .. row_ptr[i+1]),
+ * with log-weights val[...]; a missing edge is log 0 = -inf.  Dense
+ * emissions: the batch supplies E_t[j] = log B_j(x_t) directly.  Discrete
+ * emissions: logB[j*V + v] = log B_{j,v} and the batch supplies symbols. */
+typedef struct {
+  int32_t K;
+  const float* log_pi;     /* [K]                                   */
+  int32_t trans;           /* fv_trans_kind                         */
+  const float* logA;       /* dense [K*K]                           */
+  const int32_t* row_ptr;  /* CSR [K+1]                             */
+  const int32_t* col;      /* CSR [nnz]                             */
+  const float* val;        /* CSR [nnz]                             */
+  int64_t nnz;
+  int32_t emit;            /* fv_emit_kind                          */
+  int32_t V;               /* discrete: number of symbols           */
+  const float* logB;       /* discrete: [K*V]                       */
+} fv_model;
+
+/* A batch of sequences, each decoded under one model.  Sequence b has
+ * T[b] >= 1 steps.  Dense emissions: its row t is E[e_off[b] + t*K ..
+ * + K) (K of its model).  Discrete: its symbol t is obs[e_off[b] + t].
+ * Its path goes to paths_out[path_off[b] .. + T[b]).  The _host arrays are
+ * host copies used for planning; T_host is required by fv_workspace_size
+ * and, when given to fv_decode, lets it check the workspace at once.
+ * model_host (or model_idx) may be NULL: every sequence uses model 0. */
+typedef struct {
+  int32_t n_seq;
+  const int32_t* T_host;      /* HOST [n_seq]                    */
+  const int32_t* model_host;  /* HOST [n_seq] or NULL            */
+  const int32_t* T;           /* [n_seq]                         */
+  const int32_t* model_idx;   /* [n_seq] or NULL                 */
+  const int64_t* e_off;       /* [n_seq] elements                */
+  const float* E;             /* dense emission scores           */
+  const int32_t* obs;         /* discrete symbols                */
+  const int64_t* path_off;    /* [n_seq] elements of paths_out   */
+} fv_batch;
+
+/* mode and its knobs: P = parallelism degree of the first split (Sec.
+ * V-A.3; P < 2 means the binary root of Alg. 2), B = beam width (Sec. V-C;
+ * B >= K keeps every finite state), mem_budget_bytes = FLASH working
+ * memory the decoder may use for per-segment backpointer tables (0 = pure
+ * divide and conquer). */
+typedef struct {
+  int32_t mode;               /* fv_mode                         */
+  int32_t P;
+  int32_t B;
+  uint64_t mem_budget_bytes;
+  uint32_t flags;
+} fv_params;
+
+/* Bytes of device workspace fv_decode needs for this request (>= 4096).
+ * Returns 0 on invalid arguments. */
+size_t fv_workspace_size(const fv_model* models, int32_t n_models,
+                         const fv_batch* batch, const fv_params* params);
+
+/* Decode every sequence of the batch.  Writes paths_out (int32 state ids)
+ * and scores_out[b] (the path's log-likelihood, forward order).  The
+ * workspace must be 256-byte aligned and at least fv_workspace_size bytes;
+ * its contents on entry do not matter.  Asynchronous on `stream`. */
+fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* batch,
+                    const fv_params* params, void* workspace, size_t ws_bytes,
+                    int32_t* paths_out, float* scores_out, fv_stream_t stream);
+
+/* Gradient of L = sum_b grad_scores[b] * score_b with every path held
+ * fixed (the Viterbi score is piecewise linear in the inputs):
+ *   dlog_pi[j]    = sum_b g_b [q_{b,0} = j]
+ *   dlogA[i*K+j]  = sum_b g_b #{t >= 1: q_{b,t-1} = i, q_{b,t} = j}
+ *   dE[e_off[b] + t*K + j] = g_b [q_{b,t} = j]   (0 elsewhere)
+ * Sums run over b in ascending order, each term the FP32 product g_b*count,
+ * starting from +0, so the result is deterministic.  Dense transitions and
+ * dense emissions only; one model (n_models == 1).  dE uses E's layout and
+ * every element of it covered by the batch is written. */
+fv_status fv_backward(const fv_model* models, int32_t n_models, const fv_batch* batch,
+                      const int32_t* paths, const float* grad_scores,
+                      float* dlog_pi, float* dlogA, float* dE,
+                      void* workspace, size_t ws_bytes, fv_stream_t stream);
+
+/* Bytes of workspace fv_backward needs. */
+size_t fv_backward_workspace_size(const fv_model* models, int32_t n_models,
+                                  const fv_batch* batch);
+
+/* Status recorded on the device by the last call that used `workspace`
+ * (synchronises `stream`). */
+fv_status fv_last_device_status(const void* workspace, fv_stream_t stream);
+
+/* Static description of a status code. */
+const char* fv_status_str(fv_status s);
+
+/* Recompute score_b = log-likelihood of paths (forward order of Sec.
+ * III-A) for every sequence.  Dense or CSR transitions (a missing edge
+ * gives -inf). */
+fv_status fv_path_score(const fv_model* models, int32_t n_models, const fv_batch* batch,
+                        const int32_t* paths, float* scores_out, fv_stream_t stream);
+
+/* Optional timing of the main decode kernel, for roofline reports.  While
+ * enabled, every fv_decode records a CUDA event pair (library-owned, at most
+ * 256 pairs) around its main decode kernel launches on the call's stream.
+ * fv_timing_read synchronises on the recorded pairs and returns the total
+ * elapsed milliseconds and the number of pairs since the last reset. */
+fv_status fv_timing_enable(int32_t on);
+fv_status fv_timing_reset(void);
+fv_status fv_timing_read(float* total_ms, int32_t* n_pairs);
+
+/* Library version string. */
+const char* fv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H */

@@ -1,0 +1,81 @@
+// fv_internal.cuh -- structures and sm_103a device helpers shared by the
+// libfv translation units (workspace layout, job table, cluster/DSMEM PTX).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fv.h"
+
+namespace fv {
+
+constexpr int kMaxModels = 64;
+constexpr size_t kAlign = 256;
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// Per-sequence entry of the job table (written by the prep kernel).
+struct Job {
+  int32_t T;
+  int32_t model;
+  int64_t e_off;     // first element of the sequence in E (dense) or obs
+  int64_t path_off;  // first element in paths_out
+  int64_t aux_off;   // first element of its backpointer table / revealed scores
+};
+
+// Workspace header (first 1 KiB of every workspace).
+struct WsHeader {
+  uint32_t status;             // first fv_status != 0 recorded on the device
+  uint32_t detail;             // extra code for diagnostics
+  uint64_t aux_need;           // elements of the per-sequence aux area needed
+  uint64_t aux_cap;            // elements available
+  uint64_t counters[5];        // mode-specific counters (tasks, reruns, ...)
+  unsigned long long pop[kMaxModels];  // per-model work counters
+  uint32_t pad[(1024 - 64 - 8 * kMaxModels) / 4];
+};
+static_assert(sizeof(WsHeader) == 1024, "header must be 1 KiB");
+
+// Model table passed by value to the prep kernel.
+struct ModelK {
+  int32_t K[kMaxModels];
+};
+
+// Record the first device-side error (later errors do not overwrite it).
+__device__ inline void set_status(WsHeader* h, uint32_t st, uint32_t detail = 0) {
+  if (atomicCAS(&h->status, 0u, st) == 0u) h->detail = detail;
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ inline uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ inline void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of `p` (this CTA's shared memory) in the shared window of CTA
+// `rank` of the cluster.
+__device__ inline uint32_t dsmem_addr(const void* p, uint32_t rank) {
+  uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p)), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ inline void dsmem_st_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ inline void dsmem_st_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ inline void dsmem_st_u16(uint32_t addr, uint16_t v) {
+  asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+__device__ inline void dsmem_st_s64(uint32_t addr, long long v) {
+  asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+__device__ inline float ld_nc(const float* p) { return __ldg(p); }
+
+}  // namespace fv

@@ -1,0 +1,113 @@
+"""C-ABI boundary checks that need no GPU: the library builds, loads and
+exports every function include/fv.h declares; argument errors come back at
+once without touching the device; workspace sizes follow the documented
+layout."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2510_19301_gb300 import _lib as L
+from paper_2510_19301_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = L.declared_functions()
+    assert "fv_decode" in names and "fv_backward" in names and "fv_workspace_size" in names
+    for n in names:
+        assert hasattr(lib, n), f"libfv.so does not export {n}"
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.fv_status_str(s)
+    assert b"sm_103a" in lib.fv_version()
+
+
+FAKE = ctypes.c_void_p(0x10000)  # never dereferenced by the calls below
+
+
+def _model(K=8, dense=True):
+    m = L.fv_model()
+    m.K = K
+    m.log_pi = FAKE
+    m.trans = L.FV_TRANS_DENSE if dense else L.FV_TRANS_CSR
+    m.logA = FAKE if dense else None
+    if not dense:
+        m.row_ptr = m.col = m.val = FAKE
+        m.nnz = 4 * K
+    m.emit = L.FV_EMIT_DENSE
+    return m
+
+
+def _batch(T):
+    T = np.ascontiguousarray(np.asarray(T, np.int32))
+    b = L.fv_batch()
+    b.n_seq = len(T)
+    b.T_host = T.ctypes.data_as(ctypes.c_void_p)
+    b.T = b.e_off = b.path_off = b.E = FAKE
+    return b, T
+
+
+def _params(mode=L.FV_VANILLA, P=1, B=0):
+    p = L.fv_params()
+    p.mode, p.P, p.B = mode, P, B
+    return p
+
+
+def test_workspace_size_vanilla_layout(lib):
+    m = (L.fv_model * 1)(_model(K=10))
+    b, T = _batch([3, 1, 17])
+    sz = lib.fv_workspace_size(m, 1, ctypes.byref(b), ctypes.byref(_params()))
+    aux = sum(((t * 10 + 7) // 8) * 8 for t in T) * 2
+    assert sz >= aux and sz % 256 == 0
+    b2, _ = _batch([3, 1, 18])
+    assert lib.fv_workspace_size(m, 1, ctypes.byref(b2), ctypes.byref(_params())) >= sz
+
+
+def test_argument_errors_return_at_once(lib):
+    m = (L.fv_model * 1)(_model())
+    b, T = _batch([4, 5])
+    p = _params()
+    ws = ctypes.c_void_p(0x100000)
+    # null models / batch / params
+    assert lib.fv_decode(None, 1, ctypes.byref(b), ctypes.byref(p), ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
+    assert lib.fv_decode(m, 1, None, ctypes.byref(p), ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
+    assert lib.fv_decode(m, 1, ctypes.byref(b), None, ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
+    # T < 1
+    bad, _ = _batch([4, 0])
+    assert lib.fv_decode(m, 1, ctypes.byref(bad), ctypes.byref(p), ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
+    assert lib.fv_workspace_size(m, 1, ctypes.byref(bad), ctypes.byref(p)) == 0
+    # unaligned workspace
+    assert lib.fv_decode(m, 1, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(0x100010), 1 << 20,
+                         FAKE, FAKE, None) == L.FV_EINVAL
+    # workspace too small for the declared lengths (checked on the host)
+    long_b, _ = _batch([4000, 5000])
+    assert lib.fv_decode(m, 1, ctypes.byref(long_b), ctypes.byref(p), ws, 8192, FAKE, FAKE, None) == L.FV_ENOMEM
+    # K out of range
+    big = (L.fv_model * 1)(_model(K=70000))
+    assert lib.fv_decode(big, 1, ctypes.byref(b), ctypes.byref(p), ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
+    # bad mode and knobs
+    assert lib.fv_decode(m, 1, ctypes.byref(b), ctypes.byref(_params(mode=7)), ws, 1 << 20, FAKE, FAKE,
+                         None) == L.FV_EINVAL
+    assert lib.fv_decode(m, 1, ctypes.byref(b), ctypes.byref(_params(mode=L.FV_FLASH, P=0)), ws, 1 << 20,
+                         FAKE, FAKE, None) == L.FV_EINVAL
+    assert lib.fv_decode(m, 1, ctypes.byref(b), ctypes.byref(_params(mode=L.FV_BEAM, B=0)), ws, 1 << 20,
+                         FAKE, FAKE, None) == L.FV_EINVAL
+    # several models need per-sequence model indices
+    m2 = (L.fv_model * 2)(_model(), _model())
+    assert lib.fv_decode(m2, 2, ctypes.byref(b), ctypes.byref(p), ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
+
+
+def test_empty_batch_is_ok_without_device_work(lib):
+    m = (L.fv_model * 1)(_model())
+    b, _ = _batch([])
+    p = _params()
+    assert lib.fv_decode(m, 1, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(0x100000), 1 << 20,
+                         None, None, None) == L.FV_OK
