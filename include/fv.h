@@ -173,6 +173,32 @@ fv_status fv_timing_enable(int32_t on);
 fv_status fv_timing_reset(void);
 fv_status fv_timing_read(float* total_ms, int32_t* n_pairs);
 
+/* Bytes of the static device scratch behind fv_decode_noalloc. */
+#define FV_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Exact decoding (mode FV_VANILLA, dense transitions) without any device
+ * allocation, for callers that may not allocate device memory at decode
+ * time: code held to a memory budget fixed at start-up, plug-ins whose host
+ * owns the device allocator, or latency-critical paths where an allocation
+ * could block.  The paper has no counterpart to this entry point.
+ *
+ * Same inputs, outputs and results as fv_decode with mode FV_VANILLA, but
+ * the scratch lives in a file-scope device array of
+ * FV_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library holds
+ * until the process exits.  batch->T_host is required; a request whose
+ * workspace (fv_workspace_size for FV_VANILLA) exceeds that size is rejected
+ * with FV_ENOMEM before anything is enqueued.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array, so calls that overlap
+ * on the GPU (two streams, two threads) race and corrupt each other's
+ * results: serialise them.  Device-side errors are recorded inside the
+ * shared scratch and are not reported by this entry point. */
+fv_status fv_decode_noalloc(const fv_model* models, int32_t n_models, const fv_batch* batch,
+                            int32_t* paths_out, float* scores_out, fv_stream_t stream);
+
 /* Library version string. */
 const char* fv_version(void);
 

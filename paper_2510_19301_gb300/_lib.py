@@ -117,6 +117,8 @@ def load(build_if_missing: bool = False):
     lib.fv_timing_reset.restype = ctypes.c_int
     lib.fv_timing_read.argtypes = [P, P]
     lib.fv_timing_read.restype = ctypes.c_int
+    lib.fv_decode_noalloc.argtypes = [MP, i32, BP, P, P, P]
+    lib.fv_decode_noalloc.restype = ctypes.c_int
     lib.fv_version.argtypes = []
     lib.fv_version.restype = ctypes.c_char_p
     _lib = lib
