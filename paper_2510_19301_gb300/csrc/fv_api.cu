@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <unordered_map>
 #include <vector>
 
 #include "fv_internal.cuh"
@@ -15,18 +17,126 @@ using namespace fv;
 
 namespace {
 
-struct Layout {
-  size_t hdr, jobs, order, qlast, aux, prefix;
+// Per-model sequence ranges of the model-major order.
+struct Ranges {
+  std::vector<int32_t> count, begin;
 };
 
-Layout layout_for(int32_t n_seq) {
+Ranges model_ranges(const fv_batch* b, int32_t n_models) {
+  Ranges r;
+  r.count.assign(n_models, 0);
+  r.begin.assign(n_models, 0);
+  if (b->model_host) {
+    for (int i = 0; i < b->n_seq; ++i) r.count[b->model_host[i]]++;
+  } else {
+    r.count[0] = b->n_seq;
+  }
+  for (int m = 1; m < n_models; ++m) r.begin[m] = r.begin[m - 1] + r.count[m - 1];
+  return r;
+}
+
+int32_t pe_host(int32_t T, int32_t P) {
+  if (T <= 1) return 1;
+  int32_t p = P < 2 ? 2 : P;
+  return p < T ? p : T;
+}
+
+// Tasks per level below a segment of length L (index 0 = the segment's own
+// level), following the children rule of Alg. 1.
+const std::vector<int64_t>& level_counts(int64_t L, std::unordered_map<int64_t, std::vector<int64_t>>& memo) {
+  auto it = memo.find(L);
+  if (it != memo.end()) return it->second;
+  std::vector<int64_t> r;
+  if (L >= 2) {
+    r.push_back(1);
+    const int64_t d = L - 1, left = d / 2 + 1, right = L - left;
+    auto add = [&](int64_t len) {
+      const std::vector<int64_t>& c = level_counts(len, memo);
+      if (r.size() < c.size() + 1) r.resize(c.size() + 1, 0);
+      for (size_t k = 0; k < c.size(); ++k) r[k + 1] += c[k];
+    };
+    if (d > 2) { add(left); add(right); }
+    else if (d == 2) add(left);
+  }
+  return memo.emplace(L, std::move(r)).first->second;
+}
+
+struct FlashPlan {
+  std::vector<int32_t> levels;      // per model: number of subtask levels
+  std::vector<int64_t> max_tasks;   // per model: largest level
+  int64_t list_cap = 0;             // entries per task list (max over models, >= level-1 lists)
+  int32_t pe_max = 1, k_max = 1;
+};
+
+FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b, int32_t P) {
+  FlashPlan fp;
+  fp.levels.assign(n_models, 0);
+  fp.max_tasks.assign(n_models, 0);
+  std::vector<std::vector<int64_t>> per(n_models);
+  std::unordered_map<int64_t, std::vector<int64_t>> memo;
+  for (int i = 0; i < b->n_seq; ++i) {
+    const int m = b->model_host ? b->model_host[i] : 0;
+    const int32_t T = b->T_host[i], Pe = pe_host(T, P);
+    if (Pe > fp.pe_max) fp.pe_max = Pe;
+    int32_t prev = -1;
+    for (int k = 0; k < Pe; ++k) {
+      const int32_t e = (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
+      const std::vector<int64_t>& c = level_counts(e - prev, memo);
+      if (per[m].size() < c.size()) per[m].resize(c.size(), 0);
+      for (size_t l = 0; l < c.size(); ++l) per[m][l] += c[l];
+      prev = e;
+    }
+  }
+  for (int m = 0; m < n_models; ++m) {
+    if (models[m].K > fp.k_max) fp.k_max = models[m].K;
+    fp.levels[m] = (int32_t)per[m].size();
+    for (int64_t c : per[m]) fp.max_tasks[m] = std::max(fp.max_tasks[m], c);
+    fp.list_cap = std::max(fp.list_cap, fp.max_tasks[m]);
+  }
+  fp.list_cap = std::max<int64_t>(fp.list_cap, b->n_seq);
+  return fp;
+}
+
+struct Layout {
+  size_t hdr, jobs, order, qlast, aux, maps, snaps, listA, listB, pos, bsum, counts, total;
+  uint64_t aux_elems;
+  int64_t map_stride, snap_stride, list_cap;
+};
+
+// Workspace layout of a request; fp only for FV_FLASH.  aux_elems = elements
+// of the per-sequence aux area (vanilla: uint16 psi; flash: float delta).
+Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, int mode, const FlashPlan* fp) {
   Layout L;
+  memset(&L, 0, sizeof(L));
+  const int32_t n = b->n_seq;
   L.hdr = 0;
   L.jobs = align_up(sizeof(WsHeader));
-  L.order = align_up(L.jobs + sizeof(Job) * (size_t)n_seq);
-  L.qlast = align_up(L.order + sizeof(int32_t) * (size_t)n_seq);
-  L.aux = align_up(L.qlast + sizeof(int32_t) * (size_t)n_seq);
-  L.prefix = L.aux;
+  L.order = align_up(L.jobs + sizeof(Job) * (size_t)n);
+  L.qlast = align_up(L.order + sizeof(int32_t) * (size_t)n);
+  L.aux = align_up(L.qlast + sizeof(int32_t) * (size_t)n);
+  uint64_t aux = 0;
+  for (int i = 0; i < n && b->T_host; ++i) {
+    const int m = b->model_host ? b->model_host[i] : 0;
+    const uint64_t T = (uint64_t)b->T_host[i], K = (uint64_t)models[m].K;
+    if (mode == FV_VANILLA) aux += (T * K + 7ull) & ~7ull;
+    else aux += (T + 3ull) & ~3ull;
+  }
+  L.aux_elems = aux;
+  size_t end = align_up(L.aux + aux * (mode == FV_VANILLA ? 2 : 4));
+  if (mode == FV_FLASH && fp) {
+    L.map_stride = (int64_t)(fp->pe_max > 1 ? fp->pe_max - 1 : 1) * fp->k_max;
+    L.snap_stride = (int64_t)fp->pe_max * fp->k_max;
+    L.list_cap = fp->list_cap;
+    L.maps = end;
+    L.snaps = align_up(L.maps + sizeof(uint16_t) * (size_t)L.map_stride * n);
+    L.listA = align_up(L.snaps + sizeof(float) * (size_t)L.snap_stride * n);
+    L.listB = align_up(L.listA + sizeof(Task) * (size_t)L.list_cap);
+    L.pos = align_up(L.listB + sizeof(Task) * (size_t)L.list_cap);
+    L.bsum = align_up(L.pos + sizeof(int32_t) * (size_t)L.list_cap);
+    L.counts = align_up(L.bsum + sizeof(int32_t) * (size_t)(L.list_cap / 256 + 2));
+    end = align_up(L.counts + 64);
+  }
+  L.total = end < 4096 ? 4096 : end;
   return L;
 }
 
@@ -71,19 +181,6 @@ fv_status check_common(const fv_model* models, int32_t n_models, const fv_batch*
   return FV_OK;
 }
 
-// Elements of the per-sequence aux area for a mode (must match prep_kernel).
-uint64_t aux_need(const fv_model* models, const fv_batch* b, int mode) {
-  uint64_t need = 0;
-  for (int i = 0; i < b->n_seq; ++i) {
-    const int m = b->model_host ? b->model_host[i] : 0;
-    const uint64_t T = (uint64_t)b->T_host[i], K = (uint64_t)models[m].K;
-    if (mode == FV_VANILLA) need += (T * K + 7ull) & ~7ull;
-  }
-  return need;
-}
-
-size_t aux_elem_bytes(int mode) { return mode == FV_VANILLA ? 2 : 4; }
-
 // Library-owned event pairs around the main decode kernel (timing hook).
 constexpr int kMaxTimed = 256;
 bool g_timing = false;
@@ -124,10 +221,12 @@ size_t fv_workspace_size(const fv_model* models, int32_t n_models, const fv_batc
                          const fv_params* p) {
   if (!p || !batch || !batch->T_host) return 0;
   if (check_common(models, n_models, batch) != FV_OK) return 0;
-  const Layout L = layout_for(batch->n_seq);
-  size_t total = L.prefix + aux_need(models, batch, p->mode) * aux_elem_bytes(p->mode);
-  total = align_up(total);
-  return total < 4096 ? 4096 : total;
+  if (p->mode == FV_FLASH) {
+    if (p->P < 1) return 0;
+    const FlashPlan fp = plan_flash(models, n_models, batch, p->P);
+    return layout_for(models, n_models, batch, p->mode, &fp).total;
+  }
+  return layout_for(models, n_models, batch, p->mode, nullptr).total;
 }
 
 fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p,
@@ -142,15 +241,18 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   if (p->mode != FV_VANILLA && p->mode != FV_FLASH && p->mode != FV_BEAM) return FV_EINVAL;
   if (p->mode == FV_FLASH && p->P < 1) return FV_EINVAL;
   if (p->mode == FV_BEAM && (p->B < 1 || p->P < 0)) return FV_EINVAL;
-  if (p->mode != FV_VANILLA) return FV_EUNSUPPORTED;
+  if (p->mode == FV_BEAM) return FV_EUNSUPPORTED;
+  if (p->mode == FV_FLASH && !batch->T_host) return FV_EINVAL;  // levels are planned from host lengths
   for (int m = 0; m < n_models; ++m)
     if (models[m].trans != FV_TRANS_DENSE || !dense_supported_K(models[m].K)) return FV_EUNSUPPORTED;
 
   const int32_t n = batch->n_seq;
-  const Layout L = layout_for(n);
-  if (ws_bytes < L.prefix) return FV_ENOMEM;
-  const uint64_t cap = (ws_bytes - L.prefix) / aux_elem_bytes(p->mode);
-  if (batch->T_host && aux_need(models, batch, p->mode) > cap) return FV_ENOMEM;
+  FlashPlan fp;
+  if (p->mode == FV_FLASH) fp = plan_flash(models, n_models, batch, p->P);
+  const Layout L = layout_for(models, n_models, batch, p->mode, p->mode == FV_FLASH ? &fp : nullptr);
+  if (batch->T_host && ws_bytes < L.total) return FV_ENOMEM;
+  if (ws_bytes < L.aux) return FV_ENOMEM;
+  const uint64_t cap = (ws_bytes - L.aux) / (p->mode == FV_VANILLA ? 2 : 4);
   if (n == 0) return FV_OK;
 
   char* ws = static_cast<char*>(workspace);
@@ -158,16 +260,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   Job* jobs = reinterpret_cast<Job*>(ws + L.jobs);
   int32_t* order = reinterpret_cast<int32_t*>(ws + L.order);
   int32_t* qlast = reinterpret_cast<int32_t*>(ws + L.qlast);
-  uint16_t* psi = reinterpret_cast<uint16_t*>(ws + L.aux);
-
-  // per-model sequence ranges of the (model-major) order
-  std::vector<int32_t> count(n_models, 0), begin(n_models, 0);
-  if (batch->model_host) {
-    for (int i = 0; i < n; ++i) count[batch->model_host[i]]++;
-  } else {
-    count[0] = n;
-  }
-  for (int m = 1; m < n_models; ++m) begin[m] = begin[m - 1] + count[m - 1];
+  const Ranges R = model_ranges(batch, n_models);
 
   PrepArgs pa;
   memset(&pa, 0, sizeof(pa));
@@ -178,15 +271,15 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   pa.n_seq = n;
   pa.n_models = n_models;
   for (int m = 0; m < n_models; ++m) pa.mk.K[m] = models[m].K;
-  pa.aux_kind = 1;
+  pa.aux_kind = p->mode == FV_VANILLA ? 1 : 2;
   pa.jobs = jobs;
   pa.hdr = hdr;
-  pa.aux_cap = cap;
+  pa.aux_cap = p->mode == FV_VANILLA ? cap : L.aux_elems;
   if (launch_prep(pa, st) != cudaSuccess) return FV_ECUDA;
   if (launch_order(jobs, n, (p->flags & FV_NO_SORT) ? 1 : 0, order, st) != cudaSuccess) return FV_ECUDA;
 
   for (int m = 0; m < n_models; ++m) {
-    if (!count[m]) continue;
+    if (!R.count[m]) continue;
     const fv_model& md = models[m];
     DenseArgs da;
     memset(&da, 0, sizeof(da));
@@ -200,18 +293,66 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
     da.obs = batch->obs;
     da.jobs = jobs;
     da.order = order;
-    da.order_begin = begin[m];
-    da.order_count = count[m];
+    da.order_begin = R.begin[m];
+    da.order_count = R.count[m];
+    da.max_jobs = R.count[m];
     da.pop = &hdr->pop[m];
-    da.psi = psi;
     da.qlast = qlast;
     da.scores = scores_out;
+    da.paths = paths_out;
+    da.P = p->P;
+    da.complete = (p->flags & FV_COMPLETE_PRUNING) ? 1 : 0;
     da.hdr = hdr;
+    if (p->mode == FV_VANILLA) {
+      uint16_t* psi = reinterpret_cast<uint16_t*>(ws + L.aux);
+      da.kind = kJobVanilla;
+      da.psi = psi;
+      timed_begin(st);
+      if (launch_dense_forward(da, 0, st) != cudaSuccess) return FV_ECUDA;
+      timed_end(st);
+      if (launch_backtrack(jobs, order, R.begin[m], R.count[m], md.K, psi, qlast, paths_out, hdr, st) != cudaSuccess)
+        return FV_ECUDA;
+      continue;
+    }
+    // ---- FLASH: root pass, resolve, then the task levels of Alg. 1
+    float* sval = reinterpret_cast<float*>(ws + L.aux);
+    uint16_t* maps = reinterpret_cast<uint16_t*>(ws + L.maps);
+    float* snaps = reinterpret_cast<float*>(ws + L.snaps);
+    Task* lists[2] = {reinterpret_cast<Task*>(ws + L.listA), reinterpret_cast<Task*>(ws + L.listB)};
+    int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
+    ScanTmp tmp;
+    tmp.pos = reinterpret_cast<int32_t*>(ws + L.pos);
+    tmp.bsum = reinterpret_cast<int32_t*>(ws + L.bsum);
+    da.sval = sval;
+    da.maps = maps;
+    da.snaps = snaps;
+    da.map_stride = L.map_stride;
+    da.snap_stride = L.snap_stride;
+    da.kind = kJobRoot;
     timed_begin(st);
+    if (m > 0 && launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
     if (launch_dense_forward(da, 0, st) != cudaSuccess) return FV_ECUDA;
-    timed_end(st);
-    if (launch_backtrack(jobs, order, begin[m], count[m], md.K, psi, qlast, paths_out, hdr, st) != cudaSuccess)
+    if (launch_flash_resolve(jobs, order, R.begin[m], R.count[m], md.K, p->P, maps, snaps, L.map_stride,
+                             L.snap_stride, paths_out, sval, scores_out, hdr, st) != cudaSuccess)
       return FV_ECUDA;
+    if (fp.levels[m] > 0 &&
+        launch_level1_tasks(jobs, order, R.begin[m], R.count[m], p->P, lists[0], &counts[0], tmp, st) != cudaSuccess)
+      return FV_ECUDA;
+    int c = 0;
+    for (int lvl = 0; lvl < fp.levels[m]; ++lvl) {
+      if (launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
+      da.kind = kJobSub;
+      da.tasks = lists[c];
+      da.task_count = &counts[c];
+      da.max_jobs = (int32_t)fp.max_tasks[m];
+      if (launch_dense_forward(da, 0, st) != cudaSuccess) return FV_ECUDA;
+      if (lvl + 1 < fp.levels[m] &&
+          launch_child_tasks(lists[c], &counts[c], (int32_t)fp.max_tasks[m], lists[c ^ 1], &counts[c ^ 1], tmp,
+                             nullptr, st) != cudaSuccess)
+        return FV_ECUDA;
+      c ^= 1;
+    }
+    timed_end(st);
   }
   return FV_OK;
 }

@@ -140,17 +140,37 @@ __global__ void __launch_bounds__(256) order_kernel(const Job* jobs, int32_t n, 
 }
 
 // ------------------------------------------------------------ forward engine
-
-
 enum SlotState : int32_t { kNeedPop = 0, kWaiting = 1, kRun = 2, kDone = 3 };
 
-struct Slot {
-  int32_t state, b, t, T;
-  int64_t e_off, aux_off;
-  int32_t term, tb;
-  int32_t pb, pT;  // pending sequence popped by rank 0 (written into every CTA)
-  int64_t pe_off, paux_off;
+// A job as seen by a slot; rank 0 of the cluster fills it and copies it
+// word by word into every CTA, so all CTAs run identical slot states.
+struct PJob {
+  int32_t valid, b, m, n, T, Pe, q_prev, q_n;
+  float s_prev;
+  int32_t pad;
+  int64_t e_off, path_off, aux_off;
 };
+static_assert(sizeof(PJob) % 4 == 0, "PJob is copied as 32-bit words");
+
+struct Slot {
+  int32_t state, term, t;
+  int32_t kdiv, ediv, eprev;  // root: next division point index / value, previous one (-1: none)
+  int32_t tmid;               // sub: midpoint of the segment
+  int32_t f_mid;              // this tick: 0 no MidState, 1 MidState = psi, 2 MidState = MidState_prev[psi]
+  int32_t f_snap, f_map, f_k; // this tick: snapshot delta / store ancestor map / division index
+  int32_t pad;
+  PJob cur, pend;
+};
+
+__host__ __device__ inline int32_t flash_pe(int32_t T, int32_t P) {
+  if (T <= 1) return 1;
+  int32_t p = P < 2 ? 2 : P;
+  return p < T ? p : T;
+}
+// Division point e_k = floor(((k+1)T - 1) / P') of the P-way first split.
+__host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
+  return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
+}
 
 template <int J, int S, int NW, int CL>
 struct DenseCfg {
@@ -162,7 +182,9 @@ struct DenseCfg {
   static_assert((S * J) % NT == 0, "epilogue outputs per thread");
   static size_t smem_bytes(int KP) {
     const int KPS = KP + KP / 32;
-    return sizeof(float) * ((size_t)KP * J + 2ull * KP * S + 2ull * S * KPS + (size_t)NW * S * J);
+    return sizeof(float) * ((size_t)KP * J + 2ull * KP * S + 2ull * S * KPS + (size_t)NW * S * J +
+                            (size_t)S * KP) +
+           sizeof(uint16_t) * 2ull * S * KP;
   }
 };
 
@@ -174,26 +196,30 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
   __shared__ Slot slots[S];
 
   const int K = a.K, KP = a.KP, C = KP / NW, KPS = KP + KP / 32;
-  float* sA = smem;                  // [KP][J]    logA column slab
-  float* sD = sA + (size_t)KP * J;   // [2][KP][S] delta, row-major in i
-  float* sR = sD + 2 * KP * S;       // [2][S][KPS] delta per slot, skewed
-  float* sPart = sR + 2 * S * KPS;   // [NW][S][J] per-warp partial maxima
+  float* sA = smem;                  // [KP][J]     logA column slab
+  float* sD = sA + (size_t)KP * J;   // [2][KP][S]  delta, row-major in i
+  float* sR = sD + 2 * KP * S;       // [2][S][KPS] delta per slot, bank-skewed
+  float* sPart = sR + 2 * S * KPS;   // [NW][S][J]  per-warp partial maxima
+  float* sSnap = sPart + NW * S * J; // [S][KP]     sub: delta at t_mid
+  uint16_t* sMid = reinterpret_cast<uint16_t*>(sSnap + S * KP);  // [2][S][KP] MidState
 
   const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
   const int j0 = (int)rank * J;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kind = a.kind;
 
-  if (a.hdr->status != 0) return;  // prep found an error: do nothing
+  if (a.hdr->status != 0) return;  // an earlier kernel recorded an error: do nothing
 
   for (int x = tid; x < KP * J; x += NT) {
     const int i = x / J, j = j0 + x % J;
     sA[x] = (i < K && j < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
   }
   for (int x = tid; x < 2 * KP * S + 2 * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
+  for (int x = tid; x < 2 * S * KP; x += NT) sMid[x] = 0;
   if (tid < S) {
     slots[tid].state = kNeedPop;
     slots[tid].term = 0;
-    slots[tid].pb = -1;
+    slots[tid].pend.valid = 0;
   }
   if (CL > 1) cluster_sync_all(); else __syncthreads();
 
@@ -203,18 +229,18 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
     if (tid < S) {
       Slot& sl = slots[tid];
       sl.term = 0;
-      if (sl.state == kRun && sl.t >= sl.T) {
-        sl.term = 1;
-        sl.tb = sl.b;
+      if (sl.state == kRun && sl.t > sl.cur.n) {
+        sl.term = 1;  // sl.cur stays valid for the termination below
         sl.state = kNeedPop;
       } else if (sl.state == kWaiting) {
-        if (sl.pb >= 0) {
+        if (sl.pend.valid) {
+          sl.cur = sl.pend;
           sl.state = kRun;
-          sl.b = sl.pb;
-          sl.T = sl.pT;
-          sl.e_off = sl.pe_off;
-          sl.aux_off = sl.paux_off;
-          sl.t = 0;
+          sl.t = sl.cur.m;
+          sl.kdiv = 0;
+          sl.ediv = flash_div(0, sl.cur.T, sl.cur.Pe);
+          sl.eprev = -1;
+          sl.tmid = (sl.cur.m + sl.cur.n) / 2;
         } else {
           sl.state = kDone;
         }
@@ -222,52 +248,103 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
       if (sl.state == kNeedPop) {
         if (rank == 0) {
           const unsigned long long k = atomicAdd(a.pop, 1ull);
-          int32_t nb = -1, nT = 0;
-          int64_t ne = 0, na = 0;
-          if (k < (unsigned long long)a.order_count) {
-            nb = a.order[a.order_begin + (int)k];
-            const Job jb = a.jobs[nb];
-            nT = jb.T;
-            ne = jb.e_off;
-            na = jb.aux_off;
-          }
-          for (int r = 0; r < CL; ++r) {
-            if (r == 0) {
-              sl.pb = nb; sl.pT = nT; sl.pe_off = ne; sl.paux_off = na;
-            } else {
-              dsmem_st_u32(dsmem_addr(&sl.pb, r), (uint32_t)nb);
-              dsmem_st_u32(dsmem_addr(&sl.pT, r), (uint32_t)nT);
-              dsmem_st_s64(dsmem_addr(&sl.pe_off, r), ne);
-              dsmem_st_s64(dsmem_addr(&sl.paux_off, r), na);
+          PJob pj;
+          pj.valid = 0;
+          pj.b = pj.m = pj.n = pj.T = pj.Pe = pj.q_prev = pj.q_n = pj.pad = 0;
+          pj.s_prev = 0.f;
+          pj.e_off = pj.path_off = pj.aux_off = 0;
+          if (kind != kJobSub) {
+            if (k < (unsigned long long)a.order_count) {
+              const int b = a.order[a.order_begin + (int)k];
+              const Job jb = a.jobs[b];
+              pj.valid = 1;
+              pj.b = b;
+              pj.m = 0;
+              pj.n = jb.T - 1;
+              pj.T = jb.T;
+              pj.Pe = flash_pe(jb.T, a.P);
+              pj.e_off = jb.e_off;
+              pj.path_off = jb.path_off;
+              pj.aux_off = jb.aux_off;
             }
+          } else if (k < (unsigned long long)*a.task_count) {
+            const Task tk = a.tasks[k];
+            const Job jb = a.jobs[tk.b];
+            pj.valid = 1;
+            pj.b = tk.b;
+            pj.m = tk.m;
+            pj.n = tk.n;
+            pj.T = jb.T;
+            pj.e_off = jb.e_off;
+            pj.path_off = jb.path_off;
+            pj.aux_off = jb.aux_off;
+            // states revealed by earlier levels; clamped so that no value can
+            // index shared memory outside the slab
+            const int qn = a.paths[jb.path_off + tk.n];
+            pj.q_n = (unsigned)qn < (unsigned)a.K ? qn : 0;
+            if (tk.m > 0) {
+              const int qp = a.paths[jb.path_off + tk.m - 1];
+              pj.q_prev = (unsigned)qp < (unsigned)a.K ? qp : 0;
+              pj.s_prev = a.sval[jb.aux_off + tk.m - 1];
+            }
+          }
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(&pj);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(&sl.pend);
+          for (int w = 0; w < (int)(sizeof(PJob) / 4); ++w) {
+            dst[w] = src[w];
+            for (int r = 1; r < CL; ++r) dsmem_st_u32(dsmem_addr(dst + w, r), src[w]);
           }
         }
         sl.state = kWaiting;
+      }
+      // per-tick flags of a running job
+      sl.f_mid = sl.f_snap = sl.f_map = sl.f_k = 0;
+      if (sl.state == kRun) {
+        const int t = sl.t;
+        if (kind == kJobRoot) {
+          const int is_div = (t == sl.ediv);
+          if (sl.eprev >= 0) sl.f_mid = (t == sl.eprev + 1) ? 1 : 2;
+          sl.f_snap = is_div;
+          sl.f_map = is_div && sl.kdiv >= 1;
+          sl.f_k = sl.kdiv;
+        } else if (kind == kJobSub) {
+          sl.f_mid = (t == sl.tmid + 1) ? 1 : (t > sl.tmid + 1 ? 2 : 0);
+          sl.f_snap = (t == sl.tmid);
+        }
       }
     }
     const int live = (tid < S) && (slots[tid].state != kDone || slots[tid].term);
     if (!__syncthreads_or(live)) break;
 
-    // ---- termination of sequences that finished last tick (rank 0):
-    // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q].
+    // ---- termination of jobs that finished last tick (rank 0)
     if (rank == 0) {
       for (int s = warp; s < S; s += NW) {
         if (!slots[s].term) continue;
-        float bv = -CUDART_INF_F;
-        int bi = 0x7fffffff;
-        for (int j = lane; j < K; j += 32) {
-          const float v = sD[((size_t)cur * KP + j) * S + s];
-          if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-        }
-        if (lane == 0) {
-          const int b = slots[s].tb;
-          a.qlast[b] = bi;
-          a.scores[b] = sD[((size_t)cur * KP + bi) * S + s];
+        const PJob& jb = slots[s].cur;
+        if (kind == kJobVanilla) {
+          // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q]
+          float bv = -CUDART_INF_F;
+          int bi = 0x7fffffff;
+          for (int j = lane; j < K; j += 32) {
+            const float v = sD[((size_t)cur * KP + j) * S + s];
+            if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+          }
+          if (lane == 0) {
+            a.qlast[jb.b] = bi;
+            a.scores[jb.b] = sD[((size_t)cur * KP + bi) * S + s];
+          }
+        } else if (kind == kJobSub && lane == 0) {
+          // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
+          const int tmid = (jb.m + jb.n) / 2;
+          int q = sMid[((size_t)cur * S + s) * KP + ((unsigned)jb.q_n < (unsigned)K ? jb.q_n : 0)];
+          q = (unsigned)q < (unsigned)K ? q : 0;
+          a.paths[jb.path_off + tmid] = q;
+          a.sval[jb.aux_off + tmid] = sSnap[(size_t)s * KP + q];
         }
       }
     }
@@ -282,8 +359,8 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
       const Slot& sl = slots[s];
       if (sl.state == kRun && j < K) {
         const int t = sl.t;
-        if (a.emit == FV_EMIT_DENSE) ev[r] = __ldg(a.E + sl.e_off + (int64_t)t * K + j);
-        else ev[r] = __ldg(a.logB + (int64_t)j * a.V + __ldg(a.obs + sl.e_off + t));
+        if (a.emit == FV_EMIT_DENSE) ev[r] = __ldg(a.E + sl.cur.e_off + (int64_t)t * K + j);
+        else ev[r] = __ldg(a.logB + (int64_t)j * a.V + __ldg(a.obs + sl.cur.e_off + t));
         if (t == 0) pv[r] = __ldg(a.log_pi + j);
       }
     }
@@ -321,16 +398,24 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
     }
     __syncthreads();
 
-    // ---- merge, exact argmax re-scan, + E, psi store, broadcast delta_t
+    // ---- merge, exact argmax re-scan, + E, per-kind bookkeeping, broadcast
     const int nxt = cur ^ 1;
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
       const int o = tid + r * NT, s = o / J, jj = o % J, j = j0 + jj;
       const Slot& sl = slots[s];
       if (sl.state != kRun || j >= K) continue;
+      const PJob& jb = sl.cur;
       float dval;
-      if (sl.t == 0) {
-        dval = __fadd_rn(pv[r], ev[r]);
+      int arg = 0;
+      if (sl.t == jb.m) {
+        if (jb.m == 0) {
+          dval = __fadd_rn(pv[r], ev[r]);
+        } else {
+          // pruned start (Sec. V-B.2): only transitions out of q*_{m-1}
+          const float av = sA[(size_t)jb.q_prev * J + jj];
+          dval = a.complete ? __fadd_rn(av, ev[r]) : __fadd_rn(__fadd_rn(jb.s_prev, av), ev[r]);
+        }
       } else {
         float best = sPart[(size_t)s * J + jj];
         int wb = 0;
@@ -339,7 +424,7 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
           if (v > best) { best = v; wb = w; }
         }
         const float* dr = sR + ((size_t)cur * S + s) * KPS;
-        int arg = wb * C;
+        arg = wb * C;
         float val = best;
         for (int k = C - 1; k >= 0; --k) {
           const int i = wb * C + k;
@@ -347,8 +432,26 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
           if (c == best) { arg = i; val = c; }
         }
         arg = arg < K ? arg : 0;  // only NaN inputs (unsupported) could leave it on a padded row
-        a.psi[sl.aux_off + (int64_t)sl.t * K + j] = (uint16_t)arg;
+        if (kind == kJobVanilla) a.psi[jb.aux_off + (int64_t)sl.t * K + j] = (uint16_t)arg;
         dval = __fadd_rn(val, ev[r]);
+      }
+      if (sl.f_mid) {
+        const uint16_t mnew = sl.f_mid == 1 ? (uint16_t)arg : sMid[((size_t)cur * S + s) * KP + arg];
+        uint16_t* mp = sMid + ((size_t)nxt * S + s) * KP + j;
+        *mp = mnew;
+        for (int rr = 0; rr < CL; ++rr)
+          if (rr != (int)rank) dsmem_st_u16(dsmem_addr(mp, rr), mnew);
+        if (sl.f_map) a.maps[(int64_t)jb.b * a.map_stride + (int64_t)(sl.f_k - 1) * K + j] = mnew;
+      }
+      if (sl.f_snap) {
+        if (kind == kJobRoot) {
+          a.snaps[(int64_t)jb.b * a.snap_stride + (int64_t)sl.f_k * K + j] = dval;
+        } else {
+          float* sp = sSnap + (size_t)s * KP + j;
+          *sp = dval;
+          for (int rr = 0; rr < CL; ++rr)
+            if (rr != (int)rank) dsmem_st_f32(dsmem_addr(sp, rr), dval);
+        }
       }
       float* d1 = sD + ((size_t)nxt * KP + j) * S + s;
       float* d2 = sR + ((size_t)nxt * S + s) * KPS + j + (j >> 5);
@@ -364,7 +467,15 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
       }
     }
     if (CL > 1) cluster_sync_all(); else __syncthreads();
-    if (tid < S && slots[tid].state == kRun) slots[tid].t += 1;
+    if (tid < S && slots[tid].state == kRun) {
+      Slot& sl = slots[tid];
+      if (kind == kJobRoot && sl.t == sl.ediv) {
+        sl.eprev = sl.ediv;
+        sl.kdiv += 1;
+        sl.ediv = sl.kdiv < sl.cur.Pe ? flash_div(sl.kdiv, sl.cur.T, sl.cur.Pe) : 0x7fffffff;
+      }
+      sl.t += 1;
+    }
     cur = nxt;
   }
   if (CL > 1) cluster_sync_all();
@@ -492,7 +603,7 @@ static cudaError_t launch_dense_cfg(const DenseArgs& a, int max_clusters, cudaSt
     resident = per_sm * nsm;
   }
   if (resident < 1) return cudaErrorInvalidConfiguration;
-  int want = (a.order_count + S - 1) / S;
+  int want = (a.max_jobs + S - 1) / S;
   if (max_clusters > 0 && want > max_clusters) want = max_clusters;
   const int nclu = want < resident ? want : resident;
   if (nclu < 1) return cudaSuccess;

@@ -1,0 +1,263 @@
+// fv_flash.cu -- FLASH Viterbi bookkeeping kernels around the forward engine:
+//  * resolve: after the root pass, q*_{T-1} = lowest argmax of delta_{T-1}
+//    and, walking the P'-1 ancestor maps backwards, q*_{e_k} for every
+//    division point of the P-way first split (Sec. V-A.3), with the delta
+//    value there (the retained offset used by the pruned start, Sec. V-B.2);
+//  * task lists of Alg. 1: level 1 holds the P' segments (e_{k-1}+1, e_k)
+//    of length >= 2; the children of (m, n) with t_mid = floor((m+n)/2) are
+//    (m, t_mid) and (t_mid+1, n) when n-m > 2, only (m, t_mid) when n-m = 2.
+//    Lists are built level by level (every parent before its children,
+//    tasks of one level in any order) and written in parent order through a
+//    device-wide scan, so the order is deterministic.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "fv_internal.cuh"
+#include "fv_launch.h"
+
+namespace fv {
+
+__device__ inline int32_t pe_of(int32_t T, int32_t P) {
+  if (T <= 1) return 1;
+  int32_t p = P < 2 ? 2 : P;
+  return p < T ? p : T;
+}
+__device__ inline int32_t div_of(int32_t k, int32_t T, int32_t Pe) {
+  return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
+}
+
+// One warp per sequence.
+__global__ void __launch_bounds__(128) flash_resolve_kernel(const Job* jobs, const int32_t* order, int32_t begin,
+                                                            int32_t count, int32_t K, int32_t P,
+                                                            const uint16_t* maps, const float* snaps,
+                                                            int64_t map_stride, int64_t snap_stride,
+                                                            int32_t* paths, float* sval, float* scores,
+                                                            const WsHeader* hdr) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (idx >= count || hdr->status != 0) return;
+  const int b = order[begin + idx];
+  const Job jb = jobs[b];
+  const int T = jb.T, Pe = pe_of(T, P);
+  const float* sn = snaps + (int64_t)b * snap_stride;
+  const uint16_t* mp = maps + (int64_t)b * map_stride;
+  const float* last = sn + (int64_t)(Pe - 1) * K;
+  float bv = -CUDART_INF_F;
+  int bi = 0x7fffffff;
+  for (int j = lane; j < K; j += 32) {
+    const float v = last[j];
+    if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+  }
+  if (lane != 0) return;
+  int q = bi;
+  const float score = last[q];
+  scores[b] = score;
+  paths[jb.path_off + T - 1] = q;
+  sval[jb.aux_off + T - 1] = score;
+  for (int k = Pe - 2; k >= 0; --k) {
+    q = mp[(int64_t)k * K + q];
+    q = (unsigned)q < (unsigned)K ? q : 0;
+    const int e = div_of(k, T, Pe);
+    paths[jb.path_off + e] = q;
+    sval[jb.aux_off + e] = sn[(int64_t)k * K + q];
+  }
+}
+
+// ---------------------------------------------------------------- scan
+// Pass 1: each thread's item count, exclusive scan inside the block; block
+// totals to bsum.  Pass 2 (one block): exclusive scan of bsum, total to
+// *out_count.  Pass 3: each thread writes its items at bsum[blk] + pos.
+constexpr int kScanBlock = 256;
+
+__device__ inline int block_excl_scan(int v, int* total) {
+  __shared__ int ws[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < kScanBlock / 32 ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanBlock / 32) ws[lane] = s;
+  }
+  __syncthreads();
+  const int excl = (w ? ws[w - 1] : 0) + x - v;
+  *total = ws[kScanBlock / 32 - 1];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(1024) scan_block_sums(int32_t* bsum, int32_t nblk, int32_t* out_count) {
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblk; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < nblk ? bsum[i] : 0;
+    // block-wide inclusive scan (1024 threads)
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int s = ws[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    const int incl = (w ? ws[w - 1] : 0) + x;
+    if (i < nblk) bsum[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out_count = carry;
+}
+
+// Level 1: segments of the P' split of each sequence (in `order`).
+__device__ inline int level1_count(const Job& jb, int P) {
+  const int T = jb.T, Pe = pe_of(T, P);
+  int c = 0, prev = -1;
+  for (int k = 0; k < Pe; ++k) {
+    const int e = div_of(k, T, Pe);
+    if (e - (prev + 1) >= 1) ++c;
+    prev = e;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(kScanBlock) level1_pass1(const Job* jobs, const int32_t* order, int32_t begin,
+                                                           int32_t count, int32_t P, int32_t* pos, int32_t* bsum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = i < count ? level1_count(jobs[order[begin + i]], P) : 0;
+  int total;
+  const int excl = block_excl_scan(c, &total);
+  if (i < count) pos[i] = excl;
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) level1_pass3(const Job* jobs, const int32_t* order, int32_t begin,
+                                                           int32_t count, int32_t P, const int32_t* pos,
+                                                           const int32_t* bsum, Task* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int b = order[begin + i];
+  const Job jb = jobs[b];
+  const int T = jb.T, Pe = pe_of(T, P);
+  int w = bsum[blockIdx.x] + pos[i], prev = -1;
+  for (int k = 0; k < Pe; ++k) {
+    const int e = div_of(k, T, Pe);
+    if (e - (prev + 1) >= 1) {
+      Task t;
+      t.b = b;
+      t.m = prev + 1;
+      t.n = e;
+      t.pad = 0;
+      out[w++] = t;
+    }
+    prev = e;
+  }
+}
+
+// Children of a task list (Alg. 1).
+__device__ inline int child_count(const Task& t) {
+  const int d = t.n - t.m;
+  return d > 2 ? 2 : (d == 2 ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kScanBlock) child_pass1(const Task* in, const int32_t* in_count, int32_t* pos,
+                                                          int32_t* bsum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = *in_count;
+  const int c = i < n ? child_count(in[i]) : 0;
+  int total;
+  const int excl = block_excl_scan(c, &total);
+  if (i < n) pos[i] = excl;
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) child_pass3(const Task* in, const int32_t* in_count,
+                                                          const int32_t* pos, const int32_t* bsum, Task* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *in_count) return;
+  const Task t = in[i];
+  const int c = child_count(t);
+  if (!c) return;
+  const int w = bsum[blockIdx.x] + pos[i];
+  const int tmid = (t.m + t.n) / 2;
+  Task l;
+  l.b = t.b;
+  l.m = t.m;
+  l.n = tmid;
+  l.pad = 0;
+  out[w] = l;
+  if (c == 2) {
+    Task r;
+    r.b = t.b;
+    r.m = tmid + 1;
+    r.n = t.n;
+    r.pad = 0;
+    out[w + 1] = r;
+  }
+}
+
+__global__ void reset_counter(unsigned long long* pop) { *pop = 0ull; }
+
+cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st) {
+  reset_counter<<<1, 1, 0, st>>>(pop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flash_resolve(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t K,
+                                 int32_t P, const uint16_t* maps, const float* snaps, int64_t map_stride,
+                                 int64_t snap_stride, int32_t* paths, float* sval, float* scores,
+                                 const WsHeader* hdr, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  flash_resolve_kernel<<<(count + 3) / 4, 128, 0, st>>>(jobs, order, begin, count, K, P, maps, snaps, map_stride,
+                                                        snap_stride, paths, sval, scores, hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level1_tasks(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                                Task* out, int32_t* out_count, ScanTmp tmp, cudaStream_t st) {
+  const int nblk = (count + kScanBlock - 1) / kScanBlock;
+  if (nblk == 0) return cudaSuccess;
+  level1_pass1<<<nblk, kScanBlock, 0, st>>>(jobs, order, begin, count, P, tmp.pos, tmp.bsum);
+  scan_block_sums<<<1, 1024, 0, st>>>(tmp.bsum, nblk, out_count);
+  level1_pass3<<<nblk, kScanBlock, 0, st>>>(jobs, order, begin, count, P, tmp.pos, tmp.bsum, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_child_tasks(const Task* in, const int32_t* in_count, int32_t max_in, Task* out,
+                               int32_t* out_count, ScanTmp tmp, unsigned long long* pop_reset, cudaStream_t st) {
+  const int nblk = (max_in + kScanBlock - 1) / kScanBlock;
+  if (pop_reset) reset_counter<<<1, 1, 0, st>>>(pop_reset);
+  if (nblk == 0) return cudaGetLastError();
+  child_pass1<<<nblk, kScanBlock, 0, st>>>(in, in_count, tmp.pos, tmp.bsum);
+  scan_block_sums<<<1, 1024, 0, st>>>(tmp.bsum, nblk, out_count);
+  child_pass3<<<nblk, kScanBlock, 0, st>>>(in, in_count, tmp.pos, tmp.bsum, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fv

@@ -21,6 +21,18 @@ struct PrepArgs {
   uint64_t aux_cap;  // elements available in the aux area
 };
 
+// Job kinds run by the forward engine.
+enum JobKind : int32_t {
+  kJobVanilla = 0,  // whole sequence, psi table (Sec. III-A)
+  kJobRoot = 1,     // whole sequence, P' division points (Sec. V-A.3, Alg. 2 MidState)
+  kJobSub = 2       // segment task (m, n) of Alg. 1 with the pruned start of Sec. V-B.2
+};
+
+// One divide-and-conquer task (Alg. 1 tuple) of sequence b.
+struct Task {
+  int32_t b, m, n, pad;
+};
+
 struct DenseArgs {
   int32_t K;
   int32_t KP;  // rows padded to a multiple of 4*NW (set by the launcher)
@@ -32,13 +44,25 @@ struct DenseArgs {
   const float* E;
   const int32_t* obs;
   const Job* jobs;
-  const int32_t* order;
+  int32_t kind;               // JobKind
+  const int32_t* order;       // vanilla/root: sequences in order[order_begin ..]
   int32_t order_begin;
   int32_t order_count;
+  const Task* tasks;          // sub: task list and its device-side count
+  const int32_t* task_count;
+  int32_t max_jobs;           // host upper bound of jobs (grid sizing)
   unsigned long long* pop;
-  uint16_t* psi;
-  int32_t* qlast;
-  float* scores;
+  uint16_t* psi;              // vanilla: backpointer rows at job.aux_off
+  int32_t* qlast;             // vanilla: final states
+  float* scores;              // vanilla: scores
+  int32_t* paths;             // flash: revealed states (paths_out)
+  float* sval;                // flash: delta along the path, at job.aux_off
+  uint16_t* maps;             // root: (P'-1) ancestor maps per sequence
+  float* snaps;               // root: P' delta snapshots per sequence
+  int64_t map_stride;         // elements per sequence
+  int64_t snap_stride;
+  int32_t P;
+  int32_t complete;           // offset-0 (complete pruning) start for subtasks
   WsHeader* hdr;
 };
 
@@ -61,6 +85,21 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
 cudaError_t launch_backtrack(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t K,
                              const uint16_t* psi, const int32_t* qlast, int32_t* paths, const WsHeader* hdr,
                              cudaStream_t st);
+cudaError_t launch_flash_resolve(const Job* jobs, const int32_t* order, int32_t begin, int32_t count,
+                                 int32_t K, int32_t P, const uint16_t* maps, const float* snaps,
+                                 int64_t map_stride, int64_t snap_stride, int32_t* paths, float* sval,
+                                 float* scores, const WsHeader* hdr, cudaStream_t st);
+// Level-1 tasks of Alg. 1 (the P' segments of every sequence) and the
+// children of a task list, written in parent order through a device scan.
+struct ScanTmp {
+  int32_t* pos;     // [max_items]
+  int32_t* bsum;    // [ceil(max_items / 256)]
+};
+cudaError_t launch_level1_tasks(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                                Task* out, int32_t* out_count, ScanTmp tmp, cudaStream_t st);
+cudaError_t launch_child_tasks(const Task* in, const int32_t* in_count, int32_t max_in, Task* out,
+                               int32_t* out_count, ScanTmp tmp, unsigned long long* pop_reset, cudaStream_t st);
+cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st);
 cudaError_t launch_path_score(const ScoreArgs& a, const Job* jobs, const int32_t* order, int32_t begin,
                               int32_t count, const int32_t* paths, float* scores, cudaStream_t st);
 
