@@ -98,17 +98,34 @@ FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b
 }
 
 struct Layout {
-  size_t hdr, jobs, order, qlast, aux, maps, snaps, listA, listB, pos, bsum, counts, total;
+  size_t hdr, jobs, order, qlast, aux, aux2, maps, snaps, listA, listB, pos, bsum, counts, total;
+  size_t bscratch, div_id, div_val, div_mid, div_n;
   uint64_t aux_elems;
   int64_t map_stride, snap_stride, list_cap;
+  int32_t Wcap, Bcap, pe_cap, max_ctas;
+  size_t bstride;
 };
 
-// Workspace layout of a request; fp only for FV_FLASH.  aux_elems = elements
-// of the per-sequence aux area (vanilla: uint16 psi; flash: float delta).
-Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, int mode, const FlashPlan* fp) {
+int32_t beam_wcap(const fv_model* models, int32_t n_models, int32_t B) {
+  int32_t kmax = 1;
+  for (int m = 0; m < n_models; ++m) kmax = std::max(kmax, models[m].K);
+  return std::min(std::max(B, 1), kmax);
+}
+
+// Workspace layout of a request.  fp: task-level plan (FLASH, and BEAM
+// with P >= 1).  The per-sequence aux area holds: vanilla, T*K uint16
+// backpointers; flash and FLASH-BS, T floats of delta along the path; beam
+// with P = 0, T*Wcap int32 state ids (a second area of the same size holds
+// the source slots).
+Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, int mode, const FlashPlan* fp,
+                  int32_t B = 0) {
   Layout L;
   memset(&L, 0, sizeof(L));
   const int32_t n = b->n_seq;
+  int32_t kmax = 1;
+  for (int m = 0; m < n_models; ++m) kmax = std::max(kmax, models[m].K);
+  const bool beam0 = mode == FV_BEAM && fp == nullptr;
+  if (mode == FV_BEAM) L.Wcap = beam_wcap(models, n_models, B);
   L.hdr = 0;
   L.jobs = align_up(sizeof(WsHeader));
   L.order = align_up(L.jobs + sizeof(Job) * (size_t)n);
@@ -119,22 +136,47 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
     const int m = b->model_host ? b->model_host[i] : 0;
     const uint64_t T = (uint64_t)b->T_host[i], K = (uint64_t)models[m].K;
     if (mode == FV_VANILLA) aux += (T * K + 7ull) & ~7ull;
+    else if (beam0) aux += (T * (uint64_t)L.Wcap + 3ull) & ~3ull;
     else aux += (T + 3ull) & ~3ull;
   }
   L.aux_elems = aux;
   size_t end = align_up(L.aux + aux * (mode == FV_VANILLA ? 2 : 4));
-  if (mode == FV_FLASH && fp) {
-    L.map_stride = (int64_t)(fp->pe_max > 1 ? fp->pe_max - 1 : 1) * fp->k_max;
-    L.snap_stride = (int64_t)fp->pe_max * fp->k_max;
+  if (beam0) {
+    L.aux2 = end;
+    end = align_up(L.aux2 + 4 * (size_t)aux);
+  }
+  if (fp) {
     L.list_cap = fp->list_cap;
-    L.maps = end;
-    L.snaps = align_up(L.maps + sizeof(uint16_t) * (size_t)L.map_stride * n);
-    L.listA = align_up(L.snaps + sizeof(float) * (size_t)L.snap_stride * n);
+    L.listA = end;
     L.listB = align_up(L.listA + sizeof(Task) * (size_t)L.list_cap);
     L.pos = align_up(L.listB + sizeof(Task) * (size_t)L.list_cap);
     L.bsum = align_up(L.pos + sizeof(int32_t) * (size_t)L.list_cap);
     L.counts = align_up(L.bsum + sizeof(int32_t) * (size_t)(L.list_cap / 256 + 2));
     end = align_up(L.counts + 64);
+  }
+  if (mode == FV_FLASH && fp) {
+    L.map_stride = (int64_t)(fp->pe_max > 1 ? fp->pe_max - 1 : 1) * fp->k_max;
+    L.snap_stride = (int64_t)fp->pe_max * fp->k_max;
+    L.maps = end;
+    L.snaps = align_up(L.maps + sizeof(uint16_t) * (size_t)L.map_stride * n);
+    end = align_up(L.snaps + sizeof(float) * (size_t)L.snap_stride * n);
+  }
+  if (mode == FV_BEAM) {
+    L.Bcap = fp ? kmax : L.Wcap;  // FLASH-BS subtasks may be re-run with every state
+    L.max_ctas = fv::beam_max_ctas();
+    if (L.max_ctas < 1) L.max_ctas = 1;
+    L.bstride = align_up(beam_scratch_stride(kmax, L.Bcap));
+    L.bscratch = end;
+    end = align_up(L.bscratch + L.bstride * (size_t)L.max_ctas);
+    if (fp) {
+      L.pe_cap = fp->pe_max;
+      const size_t per = (size_t)L.pe_cap * L.Wcap * n;
+      L.div_id = end;
+      L.div_val = align_up(L.div_id + 4 * per);
+      L.div_mid = align_up(L.div_val + 4 * per);
+      L.div_n = align_up(L.div_mid + 4 * per);
+      end = align_up(L.div_n + 4 * (size_t)L.pe_cap * n);
+    }
   }
   L.total = end < 4096 ? 4096 : end;
   return L;
@@ -198,6 +240,120 @@ void timed_end(cudaStream_t st) {
   ++g_timed;
 }
 
+// Beam search (P = 0) and FLASH-BS (P >= 1) launch sequence, per model.
+fv_status decode_beam(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p, char* ws,
+                      const Layout& L, const FlashPlan& fp, const Ranges& R, int32_t* paths_out, float* scores_out,
+                      cudaStream_t st) {
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + L.hdr);
+  Job* jobs = reinterpret_cast<Job*>(ws + L.jobs);
+  int32_t* order = reinterpret_cast<int32_t*>(ws + L.order);
+  int32_t* qlast = reinterpret_cast<int32_t*>(ws + L.qlast);
+  const bool tasks = p->P >= 1;
+  for (int m = 0; m < n_models; ++m) {
+    if (!R.count[m]) continue;
+    const fv_model& md = models[m];
+    BeamArgs ba;
+    memset(&ba, 0, sizeof(ba));
+    ba.K = md.K;
+    ba.trans = md.trans;
+    ba.emit = md.emit;
+    ba.V = md.V;
+    ba.log_pi = md.log_pi;
+    ba.logA = md.logA;
+    ba.row_ptr = md.row_ptr;
+    ba.col = md.col;
+    ba.val = md.val;
+    ba.logB = md.logB;
+    ba.E = batch->E;
+    ba.obs = batch->obs;
+    ba.jobs = jobs;
+    ba.order = order;
+    ba.order_begin = R.begin[m];
+    ba.order_count = R.count[m];
+    ba.pop = &hdr->pop[m];
+    ba.B = p->B;
+    ba.Wcap = L.Wcap;
+    ba.Bcap = L.Bcap;
+    ba.P = p->P;
+    ba.complete = (p->flags & FV_COMPLETE_PRUNING) ? 1 : 0;
+    ba.max_ctas = L.max_ctas;
+    ba.scratch = ws + L.bscratch;
+    ba.scratch_stride = L.bstride;
+    ba.qlast = qlast;
+    ba.scores = scores_out;
+    ba.paths = paths_out;
+    ba.hdr = hdr;
+    if (m > 0 && launch_reset(ba.pop, st) != cudaSuccess) return FV_ECUDA;
+    if (!tasks) {
+      ba.kind = kJobBeam;
+      ba.bp_id = reinterpret_cast<int32_t*>(ws + L.aux);
+      ba.bp_src = reinterpret_cast<int32_t*>(ws + L.aux2);
+      timed_begin(st);
+      if (launch_beam(ba, R.count[m], st) != cudaSuccess) return FV_ECUDA;
+      timed_end(st);
+      if (launch_beam_backtrack(jobs, order, R.begin[m], R.count[m], L.Wcap, ba.bp_id, ba.bp_src, qlast, paths_out,
+                                hdr, st) != cudaSuccess)
+        return FV_ECUDA;
+      continue;
+    }
+    // FLASH-BS: beam root with division-point beams, resolve, task levels
+    float* sval = reinterpret_cast<float*>(ws + L.aux);
+    Task* lists[2] = {reinterpret_cast<Task*>(ws + L.listA), reinterpret_cast<Task*>(ws + L.listB)};
+    int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
+    ScanTmp tmp;
+    tmp.pos = reinterpret_cast<int32_t*>(ws + L.pos);
+    tmp.bsum = reinterpret_cast<int32_t*>(ws + L.bsum);
+    ba.sval = sval;
+    ba.div_id = reinterpret_cast<int32_t*>(ws + L.div_id);
+    ba.div_val = reinterpret_cast<float*>(ws + L.div_val);
+    ba.div_mid = reinterpret_cast<int32_t*>(ws + L.div_mid);
+    ba.div_n = reinterpret_cast<int32_t*>(ws + L.div_n);
+    ba.pe_cap = L.pe_cap;
+    ba.div_stride = (int64_t)L.pe_cap * L.Wcap;
+    ba.kind = kJobRoot;
+    timed_begin(st);
+    if (launch_beam(ba, R.count[m], st) != cudaSuccess) return FV_ECUDA;
+    if (launch_beam_resolve(jobs, order, R.begin[m], R.count[m], p->P, L.Wcap, L.pe_cap, ba.div_stride, ba.div_id,
+                            ba.div_val, ba.div_mid, ba.div_n, paths_out, sval, hdr, st) != cudaSuccess)
+      return FV_ECUDA;
+    if (fp.levels[m] > 0 &&
+        launch_level1_tasks(jobs, order, R.begin[m], R.count[m], p->P, lists[0], &counts[0], tmp, st) != cudaSuccess)
+      return FV_ECUDA;
+    int c = 0;
+    for (int lvl = 0; lvl < fp.levels[m]; ++lvl) {
+      if (launch_reset(ba.pop, st) != cudaSuccess) return FV_ECUDA;
+      ba.kind = kJobSub;
+      ba.tasks = lists[c];
+      ba.task_count = &counts[c];
+      if (launch_beam(ba, (int)fp.max_tasks[m], st) != cudaSuccess) return FV_ECUDA;
+      if (lvl + 1 < fp.levels[m] &&
+          launch_child_tasks(lists[c], &counts[c], (int32_t)fp.max_tasks[m], lists[c ^ 1], &counts[c ^ 1], tmp,
+                             nullptr, st) != cudaSuccess)
+        return FV_ECUDA;
+      c ^= 1;
+    }
+    timed_end(st);
+    // score of the returned path: forward-order log-likelihood (R10)
+    ScoreArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.K = md.K;
+    sa.trans = md.trans;
+    sa.emit = md.emit;
+    sa.V = md.V;
+    sa.log_pi = md.log_pi;
+    sa.logA = md.logA;
+    sa.row_ptr = md.row_ptr;
+    sa.col = md.col;
+    sa.val = md.val;
+    sa.logB = md.logB;
+    sa.E = batch->E;
+    sa.obs = batch->obs;
+    if (launch_path_score(sa, jobs, order, R.begin[m], R.count[m], paths_out, scores_out, hdr, st) != cudaSuccess)
+      return FV_ECUDA;
+  }
+  return FV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -221,12 +377,13 @@ size_t fv_workspace_size(const fv_model* models, int32_t n_models, const fv_batc
                          const fv_params* p) {
   if (!p || !batch || !batch->T_host) return 0;
   if (check_common(models, n_models, batch) != FV_OK) return 0;
-  if (p->mode == FV_FLASH) {
-    if (p->P < 1) return 0;
+  if (p->mode == FV_FLASH || (p->mode == FV_BEAM && p->P >= 1)) {
+    if (p->P < 1 || (p->mode == FV_BEAM && p->B < 1)) return 0;
     const FlashPlan fp = plan_flash(models, n_models, batch, p->P);
-    return layout_for(models, n_models, batch, p->mode, &fp).total;
+    return layout_for(models, n_models, batch, p->mode, &fp, p->B).total;
   }
-  return layout_for(models, n_models, batch, p->mode, nullptr).total;
+  if (p->mode == FV_BEAM && p->B < 1) return 0;
+  return layout_for(models, n_models, batch, p->mode, nullptr, p->B).total;
 }
 
 fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p,
@@ -241,15 +398,16 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   if (p->mode != FV_VANILLA && p->mode != FV_FLASH && p->mode != FV_BEAM) return FV_EINVAL;
   if (p->mode == FV_FLASH && p->P < 1) return FV_EINVAL;
   if (p->mode == FV_BEAM && (p->B < 1 || p->P < 0)) return FV_EINVAL;
-  if (p->mode == FV_BEAM) return FV_EUNSUPPORTED;
-  if (p->mode == FV_FLASH && !batch->T_host) return FV_EINVAL;  // levels are planned from host lengths
-  for (int m = 0; m < n_models; ++m)
-    if (models[m].trans != FV_TRANS_DENSE || !dense_supported_K(models[m].K)) return FV_EUNSUPPORTED;
+  if (p->mode != FV_VANILLA && !batch->T_host) return FV_EINVAL;  // task levels are planned from host lengths
+  if (p->mode != FV_BEAM)
+    for (int m = 0; m < n_models; ++m)
+      if (models[m].trans != FV_TRANS_DENSE || !dense_supported_K(models[m].K)) return FV_EUNSUPPORTED;
 
   const int32_t n = batch->n_seq;
+  const bool tasks = p->mode == FV_FLASH || (p->mode == FV_BEAM && p->P >= 1);
   FlashPlan fp;
-  if (p->mode == FV_FLASH) fp = plan_flash(models, n_models, batch, p->P);
-  const Layout L = layout_for(models, n_models, batch, p->mode, p->mode == FV_FLASH ? &fp : nullptr);
+  if (tasks) fp = plan_flash(models, n_models, batch, p->P);
+  const Layout L = layout_for(models, n_models, batch, p->mode, tasks ? &fp : nullptr, p->B);
   if (batch->T_host && ws_bytes < L.total) return FV_ENOMEM;
   if (ws_bytes < L.aux) return FV_ENOMEM;
   const uint64_t cap = (ws_bytes - L.aux) / (p->mode == FV_VANILLA ? 2 : 4);
@@ -271,12 +429,15 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   pa.n_seq = n;
   pa.n_models = n_models;
   for (int m = 0; m < n_models; ++m) pa.mk.K[m] = models[m].K;
-  pa.aux_kind = p->mode == FV_VANILLA ? 1 : 2;
+  pa.aux_kind = p->mode == FV_VANILLA ? 1 : ((p->mode == FV_BEAM && !tasks) ? 3 : 2);
+  pa.aux_mult = L.Wcap;
   pa.jobs = jobs;
   pa.hdr = hdr;
   pa.aux_cap = p->mode == FV_VANILLA ? cap : L.aux_elems;
   if (launch_prep(pa, st) != cudaSuccess) return FV_ECUDA;
   if (launch_order(jobs, n, (p->flags & FV_NO_SORT) ? 1 : 0, order, st) != cudaSuccess) return FV_ECUDA;
+
+  if (p->mode == FV_BEAM) return decode_beam(models, n_models, batch, p, ws, L, fp, R, paths_out, scores_out, st);
 
   for (int m = 0; m < n_models; ++m) {
     if (!R.count[m]) continue;

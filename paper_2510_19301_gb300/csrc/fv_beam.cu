@@ -1,0 +1,633 @@
+// fv_beam.cu -- dynamic beam search (Sec. V-C) and FLASH-BS on GB300.
+//
+// One 1024-thread CTA runs one job at a time (a whole sequence, or one
+// Alg. 1 segment task) and pops the next job from a global counter.  A beam
+// is the top-B finite candidates under (score desc, state id asc); it is
+// kept sorted by state id so that the next step visits its sources in
+// ascending order.  Per step:
+//  * candidates: every target reachable from the beam gets its best source
+//    (lowest id on equal scores).  Dense transitions: one thread per target
+//    scans the beam in id order.  CSR transitions: one warp per beam entry
+//    scatters 64-bit keys (order-preserving score << 32 | ~slot) with
+//    atomicMax, so equal scores resolve to the lowest slot (= lowest id);
+//    the winning candidate value is then recomputed exactly.  A shared
+//    bitmap records the touched targets.
+//  * c_j = fl(M_j + E_t[j]); exact top-B: 4-pass MSB radix select on the
+//    order-preserving 32-bit key (-0 folded into +0), then the keys equal
+//    to the threshold are taken lowest id first (block scan in id order).
+// Beams, candidates and keys live in a per-CTA slice of the workspace.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "fv_internal.cuh"
+#include "fv_launch.h"
+
+namespace fv {
+
+constexpr int kBeamThreads = 1024;
+
+// Order-preserving map of a float to uint32 (larger float -> larger key);
+// -0 is folded into +0 so that signed zeros tie and resolve by id.
+__device__ inline uint32_t ord_key(float x) {
+  uint32_t u = __float_as_uint(x);
+  if (u == 0x80000000u) u = 0u;
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ inline int block_sum(int v, int* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  int s = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+// Exclusive block scan of v (thread order), returns the prefix; *total.
+__device__ inline int block_scan(int v, int* red, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    red[lane] = s;
+  }
+  __syncthreads();
+  const int excl = (w ? red[w - 1] : 0) + x - v;
+  *total = red[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return excl;
+}
+
+// csr weight of edge i -> j (max over duplicates), -inf if absent
+__device__ inline float beam_csr_w(const BeamArgs& a, int i, int j) {
+  int lo = a.row_ptr[i], hi = a.row_ptr[i + 1] - 1;
+  const int r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
+  while (lo <= hi) {
+    const int md = (lo + hi) >> 1;
+    const int c = a.col[md];
+    if (c < j) lo = md + 1;
+    else if (c > j) hi = md - 1;
+    else {
+      int k = md;
+      while (k > r0 && a.col[k - 1] == j) --k;
+      float best = -CUDART_INF_F;
+      for (; k < r1 && a.col[k] == j; ++k) best = fmaxf(best, a.val[k]);
+      return best;
+    }
+  }
+  return -CUDART_INF_F;
+}
+
+__device__ inline float beam_trans(const BeamArgs& a, int i, int j) {
+  return a.trans == FV_TRANS_DENSE ? __ldg(a.logA + (int64_t)i * a.K + j) : beam_csr_w(a, i, j);
+}
+
+__device__ inline float beam_emit(const BeamArgs& a, const Job& jb, int t, int j) {
+  if (a.emit == FV_EMIT_DENSE) return __ldg(a.E + jb.e_off + (int64_t)t * a.K + j);
+  return __ldg(a.logB + (int64_t)j * a.V + __ldg(a.obs + jb.e_off + t));
+}
+
+// Per-CTA scratch slice.
+struct BeamScratch {
+  float* cval;               // [K] candidate c_j
+  int32_t* cslot;            // [K] source slot in the previous beam (-1: none)
+  unsigned long long* keys;  // [K] CSR scatter keys (0 = untouched)
+  int32_t* id[2];            // [Bcap] beam state ids (sorted)
+  float* val[2];             // [Bcap] beam scores
+  int32_t* mid[2];           // [Bcap] MidState of each entry
+  int32_t* src[2];           // [Bcap] source slot of each entry (previous beam)
+  int32_t* snap_id;          // [Bcap] subtask: beam at t_mid
+  float* snap_val;           // [Bcap]
+};
+
+__device__ inline BeamScratch beam_scratch(const BeamArgs& a) {
+  BeamScratch s;
+  char* base = reinterpret_cast<char*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride;
+  const size_t K = (size_t)a.K, B = (size_t)a.Bcap;
+  s.keys = reinterpret_cast<unsigned long long*>(base);
+  base += align_up(K * 8);
+  s.cval = reinterpret_cast<float*>(base);
+  base += align_up(K * 4);
+  s.cslot = reinterpret_cast<int32_t*>(base);
+  base += align_up(K * 4);
+  for (int p = 0; p < 2; ++p) {
+    s.id[p] = reinterpret_cast<int32_t*>(base);
+    base += align_up(B * 4);
+    s.val[p] = reinterpret_cast<float*>(base);
+    base += align_up(B * 4);
+    s.mid[p] = reinterpret_cast<int32_t*>(base);
+    base += align_up(B * 4);
+    s.src[p] = reinterpret_cast<int32_t*>(base);
+    base += align_up(B * 4);
+  }
+  s.snap_id = reinterpret_cast<int32_t*>(base);
+  base += align_up(B * 4);
+  s.snap_val = reinterpret_cast<float*>(base);
+  return s;
+}
+
+size_t beam_scratch_stride(int K, int Bcap) {
+  const size_t k = (size_t)K, b = (size_t)Bcap;
+  return align_up(k * 8) + 2 * align_up(k * 4) + 10 * align_up(b * 4);
+}
+
+struct BeamSmem {
+  uint32_t* touched;  // [ceil(K/32)]
+  int* red;           // [32]
+  int* hist;          // [256]
+  int* misc;          // [8]
+};
+
+// Top-B of the touched candidates (finite only) -> beam buffer p, in id
+// order.  Returns the beam size (identical in every thread).
+__device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid) {
+  const int K = a.K, nw = (K + 31) >> 5, tid = threadIdx.x;
+  // count finite touched candidates
+  int cnt = 0;
+  for (int w = tid; w < nw; w += blockDim.x) {
+    uint32_t bits = sm.touched[w];
+    while (bits) {
+      const int j = (w << 5) + __ffs(bits) - 1;
+      bits &= bits - 1;
+      if (isfinite(S.cval[j])) ++cnt;
+    }
+  }
+  const int n_fin = block_sum(cnt, sm.red);
+  uint32_t thr = 0u;
+  int need_eq = 0;
+  const bool all = n_fin <= W;
+  if (!all) {
+    uint32_t prefix = 0u, mask = 0u;
+    int remaining = W;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      for (int k = tid; k < 256; k += blockDim.x) sm.hist[k] = 0;
+      __syncthreads();
+      for (int w = tid; w < nw; w += blockDim.x) {
+        uint32_t bits = sm.touched[w];
+        while (bits) {
+          const int j = (w << 5) + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const float c = S.cval[j];
+          if (!isfinite(c)) continue;
+          const uint32_t u = ord_key(c);
+          if ((u & mask) == prefix) atomicAdd(&sm.hist[(u >> shift) & 0xFFu], 1);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int acc = 0, d = 255;
+        for (; d > 0; --d) {
+          if (acc + sm.hist[d] >= remaining) break;
+          acc += sm.hist[d];
+        }
+        sm.misc[0] = d;
+        sm.misc[1] = remaining - acc;
+      }
+      __syncthreads();
+      prefix |= (uint32_t)sm.misc[0] << shift;
+      mask |= 0xFFu << shift;
+      remaining = sm.misc[1];
+      __syncthreads();
+    }
+    thr = prefix;
+    need_eq = remaining;  // keys == thr to take, lowest ids first
+  }
+  // selection in id order: each thread owns a contiguous block of words
+  const int per = (nw + blockDim.x - 1) / blockDim.x;
+  const int w0 = tid * per, w1 = min(nw, w0 + per);
+  int n_gt = 0, n_eq = 0;
+  for (int w = w0; w < w1; ++w) {
+    uint32_t bits = sm.touched[w];
+    while (bits) {
+      const int j = (w << 5) + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const float c = S.cval[j];
+      if (!isfinite(c)) continue;
+      if (all) { ++n_gt; continue; }
+      const uint32_t u = ord_key(c);
+      if (u > thr) ++n_gt;
+      else if (u == thr) ++n_eq;
+    }
+  }
+  int tot_eq, tot;
+  const int eq_before = block_scan(n_eq, sm.red, &tot_eq);
+  int take_eq = min(max(need_eq - eq_before, 0), n_eq);
+  const int pos = block_scan(n_gt + take_eq, sm.red, &tot);
+  int o = pos, eq_seen = 0;
+  for (int w = w0; w < w1; ++w) {
+    uint32_t bits = sm.touched[w];
+    while (bits) {
+      const int j = (w << 5) + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const float c = S.cval[j];
+      if (!isfinite(c)) continue;
+      bool take = all;
+      if (!all) {
+        const uint32_t u = ord_key(c);
+        if (u > thr) take = true;
+        else if (u == thr) take = (eq_seen++ < take_eq);
+      }
+      if (!take) continue;
+      const int sl = S.cslot[j];
+      S.id[p][o] = j;
+      S.val[p][o] = c;
+      S.src[p][o] = sl;
+      if (need_mid == 1) S.mid[p][o] = S.id[p ^ 1][sl];
+      else if (need_mid == 2) S.mid[p][o] = S.mid[p ^ 1][sl];
+      else S.mid[p][o] = -1;
+      ++o;
+    }
+  }
+  __syncthreads();
+  return tot;
+}
+
+// Clear the touched bitmap (and CSR keys of touched targets).
+__device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm) {
+  const int nw = (a.K + 31) >> 5;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    uint32_t bits = sm.touched[w];
+    if (a.trans != FV_TRANS_DENSE) {
+      while (bits) {
+        const int j = (w << 5) + __ffs(bits) - 1;
+        bits &= bits - 1;
+        S.keys[j] = 0ull;
+      }
+    }
+    sm.touched[w] = 0u;
+  }
+  __syncthreads();
+}
+
+// Candidates of step t from beam buffer p (size nb) into cval/cslot/touched.
+__device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int p, int nb, int t) {
+  const int K = a.K;
+  if (a.trans == FV_TRANS_DENSE) {
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      float best = -CUDART_INF_F;
+      int sl = -1;
+      for (int k = 0; k < nb; ++k) {
+        const float c = __fadd_rn(S.val[p][k], __ldg(a.logA + (int64_t)S.id[p][k] * K + j));
+        if (sl < 0 || c > best) { best = c; sl = k; }
+      }
+      S.cslot[j] = sl;
+      S.cval[j] = __fadd_rn(best, beam_emit(a, jb, t, j));
+      if (sl >= 0) atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+    }
+    __syncthreads();
+    return;
+  }
+  // CSR: warp per beam entry scatters keys
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int k = warp; k < nb; k += nwarp) {
+    const int i = S.id[p][k];
+    const float v = S.val[p][k];
+    for (int e = a.row_ptr[i] + lane; e < a.row_ptr[i + 1]; e += 32) {
+      const int j = a.col[e];
+      const float c = __fadd_rn(v, a.val[e]);
+      const unsigned long long key = ((unsigned long long)ord_key(c) << 32) | (0xFFFFFFFFull - (unsigned)k);
+      atomicMax(&S.keys[j], key);
+      atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+    }
+  }
+  __syncthreads();
+  const int nw = (K + 31) >> 5;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    uint32_t bits = sm.touched[w];
+    while (bits) {
+      const int j = (w << 5) + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int sl = (int)(0xFFFFFFFFull - (S.keys[j] & 0xFFFFFFFFull));
+      const float m = __fadd_rn(S.val[p][sl], beam_csr_w(a, S.id[p][sl], j));
+      S.cslot[j] = sl;
+      S.cval[j] = __fadd_rn(m, beam_emit(a, jb, t, j));
+    }
+  }
+  __syncthreads();
+}
+
+// Initial candidates at t = m: from pi (m = 0) or from the single state
+// q_prev with the retained (or zero) offset (Sec. V-B.2).
+__device__ void beam_init(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int m, int q_prev,
+                          float s_prev) {
+  const int K = a.K;
+  if (m == 0 || a.trans == FV_TRANS_DENSE) {
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      float c;
+      if (m == 0) {
+        c = __fadd_rn(__ldg(a.log_pi + j), beam_emit(a, jb, 0, j));
+      } else {
+        const float w = __ldg(a.logA + (int64_t)q_prev * K + j);
+        c = a.complete ? __fadd_rn(w, beam_emit(a, jb, m, j))
+                       : __fadd_rn(__fadd_rn(s_prev, w), beam_emit(a, jb, m, j));
+      }
+      S.cval[j] = c;
+      S.cslot[j] = 0;
+      atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+    }
+  } else {
+    for (int e = a.row_ptr[q_prev] + threadIdx.x; e < a.row_ptr[q_prev + 1]; e += blockDim.x) {
+      const int j = a.col[e];
+      // duplicates resolve to the max weight, as csr_w does
+      const float w = beam_csr_w(a, q_prev, j);
+      const float c = a.complete ? __fadd_rn(w, beam_emit(a, jb, m, j))
+                                 : __fadd_rn(__fadd_rn(s_prev, w), beam_emit(a, jb, m, j));
+      S.cval[j] = c;
+      S.cslot[j] = 0;
+      atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+    }
+  }
+  __syncthreads();
+}
+
+// Block-wide (max value, lowest index) over per-thread candidates; idx
+// 0x7fffffff marks "none".  Returns the winning index (or -1 if none or -inf).
+__device__ inline int block_argmax(float v, int idx, float* rv, int* ri) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (oi != 0x7fffffff && (idx == 0x7fffffff || ov > v || (ov == v && oi < idx))) { v = ov; idx = oi; }
+  }
+  __syncthreads();
+  if (lane == 0) { rv[w] = v; ri[w] = idx; }
+  __syncthreads();
+  float bv = -CUDART_INF_F;
+  int bi = 0x7fffffff;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+    if (ri[k] != 0x7fffffff && (bi == 0x7fffffff || rv[k] > bv || (rv[k] == bv && ri[k] < bi))) { bv = rv[k]; bi = ri[k]; }
+  }
+  __syncthreads();
+  return (bi == 0x7fffffff || !(bv > -CUDART_INF_F)) ? -1 : bi;
+}
+
+// Index of state q in an id-sorted beam (binary search), -1 if absent.
+__device__ inline int beam_find(const int32_t* ids, int nb, int q) {
+  int lo = 0, hi = nb - 1;
+  while (lo <= hi) {
+    const int md = (lo + hi) >> 1;
+    if (ids[md] == q) return md;
+    if (ids[md] < q) lo = md + 1; else hi = md - 1;
+  }
+  return -1;
+}
+
+__device__ inline int pe_b(int T, int P) {
+  if (T <= 1) return 1;
+  int p = P < 2 ? 2 : P;
+  return p < T ? p : T;
+}
+__device__ inline int div_b(int k, int T, int Pe) { return (int)((((int64_t)k + 1) * T - 1) / Pe); }
+
+__global__ void __launch_bounds__(kBeamThreads, 1) beam_kernel(BeamArgs a) {
+  extern __shared__ uint32_t bsm[];
+  __shared__ int red[32], hist[256], misc[8], ri[32];
+  __shared__ float rv[32];
+  __shared__ int s_job;
+  BeamSmem sm;
+  sm.touched = bsm;
+  sm.red = red;
+  sm.hist = hist;
+  sm.misc = misc;
+  if (a.hdr->status != 0) return;
+  BeamScratch S = beam_scratch(a);
+  const int K = a.K, nw = (K + 31) >> 5;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) sm.touched[w] = 0u;
+  if (a.trans != FV_TRANS_DENSE)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) S.keys[j] = 0ull;
+  __syncthreads();
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long k = atomicAdd(a.pop, 1ull);
+      const int lim = a.kind == kJobSub ? *a.task_count : a.order_count;
+      s_job = k < (unsigned long long)lim ? (int)k : -1;
+    }
+    __syncthreads();
+    const int jk = s_job;
+    __syncthreads();
+    if (jk < 0) break;
+    int b, m, n;
+    if (a.kind == kJobSub) {
+      const Task tk = a.tasks[jk];
+      b = tk.b;
+      m = tk.m;
+      n = tk.n;
+    } else {
+      b = a.order[a.order_begin + jk];
+      m = 0;
+      n = a.jobs[b].T - 1;
+    }
+    const Job jb = a.jobs[b];
+    const int T = jb.T;
+    int q_prev = 0, q_n = 0;
+    float s_prev = 0.f;
+    if (a.kind == kJobSub) {
+      const int qn = a.paths[jb.path_off + n];
+      q_n = (unsigned)qn < (unsigned)K ? qn : 0;
+      if (m > 0) {
+        const int qp = a.paths[jb.path_off + m - 1];
+        q_prev = (unsigned)qp < (unsigned)K ? qp : 0;
+        s_prev = a.sval[jb.aux_off + m - 1];
+      }
+    }
+    const int Pe = a.kind == kJobRoot ? pe_b(T, a.P) : 1;
+    const int tmid = (m + n) / 2;
+    bool done = false;
+    for (int attempt = 0; attempt < 2 && !done; ++attempt) {
+      // attempt 1 (subtasks only): the full state set (R9)
+      int W = attempt ? K : (a.Wcap < a.Bcap ? a.Wcap : a.Bcap);
+      if (W > a.Bcap) W = a.Bcap;
+      // ---- t = m
+      beam_init(a, S, sm, jb, m, q_prev, s_prev);
+      int p = 0;
+      int nb = select_top_b(a, S, sm, p, W, 0);
+      clear_candidates(a, S, sm);
+      int kdiv = 0, ediv = a.kind == kJobRoot ? div_b(0, T, Pe) : -1, eprev = -1, snap_n = 0;
+      bool infeasible = nb == 0;
+      // bookkeeping of step t (beam in buffer p, nb entries)
+      auto book = [&](int t) {
+        if (a.kind == kJobBeam) {
+          for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+            a.bp_id[jb.aux_off + (int64_t)t * a.Wcap + e] = S.id[p][e];
+            a.bp_src[jb.aux_off + (int64_t)t * a.Wcap + e] = t == m ? 0 : S.src[p][e];
+          }
+        } else if (a.kind == kJobRoot && t == ediv) {
+          const int64_t base = (int64_t)b * a.div_stride + (int64_t)kdiv * a.Wcap;
+          for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+            a.div_id[base + e] = S.id[p][e];
+            a.div_val[base + e] = S.val[p][e];
+            a.div_mid[base + e] = t == m ? -1 : S.mid[p][e];
+          }
+          if (threadIdx.x == 0) a.div_n[(int64_t)b * a.pe_cap + kdiv] = nb;
+          eprev = ediv;
+          ++kdiv;
+          ediv = kdiv < Pe ? div_b(kdiv, T, Pe) : 0x7fffffff;
+        } else if (a.kind == kJobSub && t == tmid) {
+          for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+            S.snap_id[e] = S.id[p][e];
+            S.snap_val[e] = S.val[p][e];
+          }
+          snap_n = nb;
+        }
+        __syncthreads();
+      };
+      if (!infeasible) book(m);
+      for (int t = m + 1; t <= n && !infeasible; ++t) {
+        if (a.kind == kJobSub && t == n) {
+          // last step: evaluate only target q_n, from every beam source (R9)
+          float bv = -CUDART_INF_F;
+          int bs = 0x7fffffff;
+          for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            const float c = __fadd_rn(S.val[p][k], beam_trans(a, S.id[p][k], q_n));
+            if (bs == 0x7fffffff || c > bv) { bv = c; bs = k; }
+          }
+          const int sidx = block_argmax(bv, bs, rv, ri);
+          if (sidx < 0) { infeasible = true; break; }
+          if (threadIdx.x == 0) {
+            const int q = (t == tmid + 1) ? S.id[p][sidx] : S.mid[p][sidx];
+            const int x = beam_find(S.snap_id, snap_n, q);
+            a.paths[jb.path_off + tmid] = (unsigned)q < (unsigned)K ? q : 0;
+            a.sval[jb.aux_off + tmid] = x >= 0 ? S.snap_val[x] : -CUDART_INF_F;
+          }
+          __syncthreads();
+          break;
+        }
+        beam_candidates(a, S, sm, jb, p, nb, t);
+        int need_mid = 0;
+        if (a.kind == kJobRoot && eprev >= 0) need_mid = (t == eprev + 1) ? 1 : 2;
+        if (a.kind == kJobSub) need_mid = (t == tmid + 1) ? 1 : (t > tmid + 1 ? 2 : 0);
+        const int np = p ^ 1;
+        nb = select_top_b(a, S, sm, np, W, need_mid);
+        clear_candidates(a, S, sm);
+        p = np;
+        if (nb == 0) { infeasible = true; break; }
+        book(t);
+      }
+      if (!infeasible) {
+        if (a.kind == kJobBeam && threadIdx.x == 0) {
+          int kb = 0;  // best final entry: highest score, lowest id
+          for (int e = 1; e < nb; ++e)
+            if (S.val[p][e] > S.val[p][kb]) kb = e;
+          a.scores[b] = S.val[p][kb];
+          a.qlast[b] = kb;
+        }
+        done = true;
+      } else if (a.kind == kJobSub && attempt == 0 && K <= a.Bcap) {
+        if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[0]), 1ull);
+      } else {
+        if (threadIdx.x == 0) set_status(a.hdr, FV_EINFEASIBLE, (uint32_t)b);
+        done = true;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Backtrack through per-step beam backpointers (one thread per sequence).
+__global__ void beam_backtrack_kernel(const Job* jobs, const int32_t* order, int32_t begin, int32_t count,
+                                      int32_t Wcap, const int32_t* bp_id, const int32_t* bp_src,
+                                      const int32_t* qlast, int32_t* paths, const WsHeader* hdr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count || hdr->status != 0) return;
+  const int b = order[begin + idx];
+  const Job jb = jobs[b];
+  int slot = qlast[b];
+  for (int t = jb.T - 1; t >= 0; --t) {
+    const int64_t base = jb.aux_off + (int64_t)t * Wcap;
+    slot = slot < 0 ? 0 : (slot >= Wcap ? Wcap - 1 : slot);
+    paths[jb.path_off + t] = bp_id[base + slot];
+    slot = bp_src[base + slot];
+  }
+}
+
+// FLASH-BS resolve: walk the stored division-point beams (one thread per
+// sequence): q_{e_{k-1}} = MidState of q_{e_k}'s entry at e_k.
+__global__ void beam_resolve_kernel(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                                    int32_t Bcap /* = Wcap */, int32_t pe_cap, int64_t div_stride, const int32_t* div_id,
+                                    const float* div_val, const int32_t* div_mid, const int32_t* div_n,
+                                    int32_t* paths, float* sval, WsHeader* hdr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count || hdr->status != 0) return;
+  const int b = order[begin + idx];
+  const Job jb = jobs[b];
+  const int T = jb.T, Pe = pe_b(T, P);
+  const int64_t base = (int64_t)b * div_stride;
+  // best entry at T-1 = e_{Pe-1}: highest score, lowest id
+  const int nlast = div_n[(int64_t)b * pe_cap + Pe - 1];
+  const int32_t* ids = div_id + base + (int64_t)(Pe - 1) * Bcap;
+  const float* vals = div_val + base + (int64_t)(Pe - 1) * Bcap;
+  if (nlast <= 0) { set_status(hdr, FV_EINFEASIBLE, (uint32_t)b); return; }
+  int kb = 0;
+  for (int e = 1; e < nlast; ++e)
+    if (vals[e] > vals[kb]) kb = e;
+  paths[jb.path_off + T - 1] = ids[kb];
+  sval[jb.aux_off + T - 1] = vals[kb];
+  int entry = kb;
+  for (int k = Pe - 1; k >= 1; --k) {
+    const int q = div_mid[base + (int64_t)k * Bcap + entry];
+    const int e = div_b(k - 1, T, Pe);
+    const int n_prev = div_n[(int64_t)b * pe_cap + k - 1];
+    const int x = beam_find(div_id + base + (int64_t)(k - 1) * Bcap, n_prev, q);
+    if (x < 0) { set_status(hdr, FV_EINFEASIBLE, (uint32_t)b); return; }
+    paths[jb.path_off + e] = q;
+    sval[jb.aux_off + e] = div_val[base + (int64_t)(k - 1) * Bcap + x];
+    entry = x;
+  }
+}
+
+cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = sizeof(uint32_t) * (size_t)((a.K + 31) / 32);
+  cudaError_t e = cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = max_jobs < a.max_ctas ? max_jobs : a.max_ctas;
+  if (grid < 1) return cudaSuccess;
+  beam_kernel<<<grid, kBeamThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_beam_backtrack(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t Wcap,
+                                  const int32_t* bp_id, const int32_t* bp_src, const int32_t* qlast, int32_t* paths,
+                                  const WsHeader* hdr, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  beam_backtrack_kernel<<<(count + 127) / 128, 128, 0, st>>>(jobs, order, begin, count, Wcap, bp_id, bp_src, qlast,
+                                                              paths, hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_beam_resolve(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                                int32_t Bcap, int32_t pe_cap, int64_t div_stride, const int32_t* div_id,
+                                const float* div_val, const int32_t* div_mid, const int32_t* div_n, int32_t* paths,
+                                float* sval, WsHeader* hdr, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  beam_resolve_kernel<<<(count + 127) / 128, 128, 0, st>>>(jobs, order, begin, count, P, Bcap, pe_cap, div_stride,
+                                                            div_id, div_val, div_mid, div_n, paths, sval, hdr);
+  return cudaGetLastError();
+}
+
+int beam_max_ctas() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+
+}  // namespace fv

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(1024) prep_kernel(PrepArgs p) {
       const unsigned long long K = (unsigned long long)p.mk.K[m];
       if (p.aux_kind == 1) need = ((unsigned long long)T * K + 7ull) & ~7ull;
       else if (p.aux_kind == 2) need = ((unsigned long long)T + 3ull) & ~3ull;
+      else if (p.aux_kind == 3) need = ((unsigned long long)T * (unsigned long long)p.aux_mult + 3ull) & ~3ull;
     }
     // block exclusive scan of need
     unsigned long long x = need;
@@ -548,9 +549,9 @@ __device__ inline float csr_weight(const ScoreArgs& a, int i, int j) {
 }
 
 __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* order, int32_t begin,
-                                  int32_t count, const int32_t* paths, float* scores) {
+                                  int32_t count, const int32_t* paths, float* scores, const WsHeader* hdr) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= count) return;
+  if (idx >= count || (hdr && hdr->status != 0)) return;
   const int b = order[begin + idx];
   const Job jb = jobs[b];
   const int32_t* q = paths + jb.path_off;
@@ -558,15 +559,19 @@ __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* o
     if (a.emit == FV_EMIT_DENSE) return __ldg(a.E + jb.e_off + (int64_t)t * a.K + j);
     return __ldg(a.logB + (int64_t)j * a.V + __ldg(a.obs + jb.e_off + t));
   };
+  // state ids outside [0, K) make the score -inf (a path through no state)
   int qp = q[0];
+  bool bad = (unsigned)qp >= (unsigned)a.K;
+  qp = bad ? 0 : qp;
   float s = __fadd_rn(__ldg(a.log_pi + qp), emis(0, qp));
   for (int t = 1; t < jb.T; ++t) {
-    const int qt = q[t];
+    int qt = q[t];
+    if ((unsigned)qt >= (unsigned)a.K) { bad = true; qt = 0; }
     const float w = a.trans == FV_TRANS_DENSE ? __ldg(a.logA + (int64_t)qp * a.K + qt) : csr_weight(a, qp, qt);
     s = __fadd_rn(__fadd_rn(s, w), emis(t, qt));
     qp = qt;
   }
-  scores[b] = s;
+  scores[b] = bad ? -CUDART_INF_F : s;
 }
 
 // ------------------------------------------------------------ host launchers
@@ -652,9 +657,10 @@ cudaError_t launch_backtrack(const Job* jobs, const int32_t* order, int32_t begi
 }
 
 cudaError_t launch_path_score(const ScoreArgs& a, const Job* jobs, const int32_t* order, int32_t begin,
-                              int32_t count, const int32_t* paths, float* scores, cudaStream_t st) {
+                              int32_t count, const int32_t* paths, float* scores, const WsHeader* hdr,
+                              cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  path_score_kernel<<<(count + 127) / 128, 128, 0, st>>>(a, jobs, order, begin, count, paths, scores);
+  path_score_kernel<<<(count + 127) / 128, 128, 0, st>>>(a, jobs, order, begin, count, paths, scores, hdr);
   return cudaGetLastError();
 }
 

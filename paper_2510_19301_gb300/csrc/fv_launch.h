@@ -15,7 +15,8 @@ struct PrepArgs {
   int32_t n_seq;
   int32_t n_models;
   ModelK mk;
-  int32_t aux_kind;  // 0: none, 1: T*K uint16 backpointers, 2: T floats
+  int32_t aux_kind;  // 0: none, 1: T*K uint16 backpointers, 2: T floats, 3: T*aux_mult int32
+  int32_t aux_mult;
   Job* jobs;
   WsHeader* hdr;
   uint64_t aux_cap;  // elements available in the aux area
@@ -25,7 +26,8 @@ struct PrepArgs {
 enum JobKind : int32_t {
   kJobVanilla = 0,  // whole sequence, psi table (Sec. III-A)
   kJobRoot = 1,     // whole sequence, P' division points (Sec. V-A.3, Alg. 2 MidState)
-  kJobSub = 2       // segment task (m, n) of Alg. 1 with the pruned start of Sec. V-B.2
+  kJobSub = 2,      // segment task (m, n) of Alg. 1 with the pruned start of Sec. V-B.2
+  kJobBeam = 3      // whole sequence, beam with per-step backpointers (Sec. V-C, P = 0)
 };
 
 // One divide-and-conquer task (Alg. 1 tuple) of sequence b.
@@ -66,6 +68,47 @@ struct DenseArgs {
   WsHeader* hdr;
 };
 
+// Beam search and FLASH-BS (fv_beam.cu).
+struct BeamArgs {
+  int32_t K, trans, emit, V;
+  const float* log_pi;
+  const float* logA;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const float* val;
+  const float* logB;
+  const float* E;
+  const int32_t* obs;
+  const Job* jobs;
+  int32_t kind;               // kJobBeam, kJobRoot or kJobSub
+  const int32_t* order;
+  int32_t order_begin, order_count;
+  const Task* tasks;
+  const int32_t* task_count;
+  unsigned long long* pop;
+  int32_t B;                  // beam width requested
+  int32_t Wcap;               // min(B, K): stride of stored beams
+  int32_t Bcap;               // scratch beam capacity (K when a subtask may be re-run exactly)
+  int32_t P;
+  int32_t complete;
+  int32_t max_ctas;
+  char* scratch;              // per CTA slice of scratch_stride bytes
+  size_t scratch_stride;
+  int32_t* bp_id;             // beam: per sequence [T][Wcap] state ids at job.aux_off
+  int32_t* bp_src;            //       and source slots
+  int32_t* qlast;             // beam: slot of the best final entry
+  float* scores;
+  int32_t* paths;             // flash-bs: revealed states
+  float* sval;                // flash-bs: beam score along the path, at job.aux_off
+  int32_t* div_id;            // root: per sequence [pe_cap][Wcap] beams at the division points
+  float* div_val;
+  int32_t* div_mid;
+  int32_t* div_n;             // root: per sequence [pe_cap] beam sizes
+  int64_t div_stride;         // pe_cap * Wcap
+  int32_t pe_cap;
+  WsHeader* hdr;
+};
+
 struct ScoreArgs {
   int32_t K, trans, emit, V;
   const float* log_pi;
@@ -100,7 +143,18 @@ cudaError_t launch_level1_tasks(const Job* jobs, const int32_t* order, int32_t b
 cudaError_t launch_child_tasks(const Task* in, const int32_t* in_count, int32_t max_in, Task* out,
                                int32_t* out_count, ScanTmp tmp, unsigned long long* pop_reset, cudaStream_t st);
 cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st);
+size_t beam_scratch_stride(int K, int Bcap);
+int beam_max_ctas();
+cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st);
+cudaError_t launch_beam_backtrack(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t Wcap,
+                                  const int32_t* bp_id, const int32_t* bp_src, const int32_t* qlast, int32_t* paths,
+                                  const WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_beam_resolve(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                                int32_t Wcap, int32_t pe_cap, int64_t div_stride, const int32_t* div_id,
+                                const float* div_val, const int32_t* div_mid, const int32_t* div_n, int32_t* paths,
+                                float* sval, WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_path_score(const ScoreArgs& a, const Job* jobs, const int32_t* order, int32_t begin,
-                              int32_t count, const int32_t* paths, float* scores, cudaStream_t st);
+                              int32_t count, const int32_t* paths, float* scores, const WsHeader* hdr,
+                              cudaStream_t st);
 
 }  // namespace fv
