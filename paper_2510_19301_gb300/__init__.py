@@ -19,8 +19,8 @@ import torch
 from . import _lib as L
 from ._lib import FVError
 
-__all__ = ["Model", "Batch", "Decoder", "decode", "path_score", "workspace_size", "FVError",
-           "MODES"]
+__all__ = ["Model", "Batch", "Decoder", "decode", "path_score", "workspace_size", "backward",
+           "ViterbiScore", "FVError", "MODES"]
 
 MODES = {"vanilla": L.FV_VANILLA, "flash": L.FV_FLASH, "beam": L.FV_BEAM}
 
@@ -216,6 +216,57 @@ def decode(models, batch, mode="vanilla", P=1, B=0, mem_budget=0, flags=0, strea
         models = [models]
     d = Decoder(models, batch, mode, P, B, mem_budget, flags)
     return d(stream, check)
+
+
+def backward(model, batch, paths, grad_scores, stream=None):
+    """Gradient of sum_b g_b * score_b with the paths held fixed:
+    (dlog_pi [K], dlogA [K, K], dE like batch.E).  Deterministic (terms
+    added in ascending sequence order)."""
+    lib = L.load()
+    arr = _models_array([model])
+    bs = batch.struct()
+    dev = batch.device
+    g = _f32(grad_scores, dev)
+    dpi = torch.empty(model.K, dtype=torch.float32, device=dev)
+    dA = torch.empty((model.K, model.K), dtype=torch.float32, device=dev)
+    dE = torch.zeros_like(batch.E)
+    wsz = int(lib.fv_backward_workspace_size(arr, 1, ctypes.byref(bs)))
+    if wsz == 0:
+        raise FVError(L.FV_EINVAL, "fv_backward_workspace_size")
+    ws = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.fv_backward(arr, 1, ctypes.byref(bs), _ptr(paths), _ptr(g), _ptr(dpi), _ptr(dA), _ptr(dE),
+                         _ptr(ws), ws.numel(), ctypes.c_void_p(st.cuda_stream))
+    if rc != L.FV_OK:
+        raise FVError(rc, "fv_backward")
+    s_ = int(lib.fv_last_device_status(_ptr(ws), ctypes.c_void_p(st.cuda_stream)))
+    if s_ != L.FV_OK:
+        raise FVError(s_, "fv_backward (device)")
+    return dpi, dA, dE
+
+
+class ViterbiScore(torch.autograd.Function):
+    """scores = ViterbiScore.apply(log_pi, logA, E, lengths[, mode, P]).
+
+    Forward decodes every sequence (FLASH by default, so only the paths are
+    kept: O(P K) working memory per sequence instead of the T x K table) and
+    returns the Viterbi scores; backward scatters the path counts
+    (structured-perceptron / CRF-style training)."""
+
+    @staticmethod
+    def forward(ctx, log_pi, logA, E, lengths, mode="flash", P=16):
+        m = Model(log_pi.detach(), logA.detach(), device=E.device)
+        b = Batch(lengths, E=E.detach().reshape(-1), models=[m], device=E.device)
+        paths, scores = decode([m], b, mode=mode, P=P)
+        ctx.save_for_backward(paths)
+        ctx.model, ctx.batch, ctx.E_shape = m, b, E.shape
+        return scores[: b.n].clone()
+
+    @staticmethod
+    def backward(ctx, grad_scores):
+        (paths,) = ctx.saved_tensors
+        dpi, dA, dE = backward(ctx.model, ctx.batch, paths, grad_scores.contiguous())
+        return dpi, dA, dE.reshape(ctx.E_shape), None, None, None
 
 
 def path_score(models, batch, paths, stream=None):

@@ -520,21 +520,75 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
 
 fv_status fv_path_score(const fv_model* models, int32_t n_models, const fv_batch* batch, const int32_t* paths,
                         float* scores_out, fv_stream_t stream_) {
-  (void)models; (void)n_models; (void)batch; (void)paths; (void)scores_out; (void)stream_;
-  return FV_EUNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream_);
+  fv_status s = check_common(models, n_models, batch);
+  if (s != FV_OK) return s;
+  if (batch->n_seq > 0 && (!paths || !scores_out)) return FV_EINVAL;
+  for (int m = 0; m < n_models; ++m) {
+    const fv_model& md = models[m];
+    ScoreArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.K = md.K;
+    sa.trans = md.trans;
+    sa.emit = md.emit;
+    sa.V = md.V;
+    sa.log_pi = md.log_pi;
+    sa.logA = md.logA;
+    sa.row_ptr = md.row_ptr;
+    sa.col = md.col;
+    sa.val = md.val;
+    sa.logB = md.logB;
+    sa.E = batch->E;
+    sa.obs = batch->obs;
+    if (launch_path_score_direct(sa, m, batch->n_seq, batch->T, batch->model_idx, batch->e_off, batch->path_off,
+                                 paths, scores_out, st) != cudaSuccess)
+      return FV_ECUDA;
+  }
+  return FV_OK;
 }
 
 size_t fv_backward_workspace_size(const fv_model* models, int32_t n_models, const fv_batch* batch) {
-  (void)models; (void)n_models; (void)batch;
-  return 0;
+  if (check_common(models, n_models, batch) != FV_OK) return 0;
+  const size_t need = align_up(sizeof(WsHeader)) + align_up(sizeof(Job) * (size_t)batch->n_seq);
+  return need < 4096 ? 4096 : need;
 }
 
 fv_status fv_backward(const fv_model* models, int32_t n_models, const fv_batch* batch, const int32_t* paths,
                       const float* grad_scores, float* dlog_pi, float* dlogA, float* dE, void* workspace,
                       size_t ws_bytes, fv_stream_t stream_) {
-  (void)models; (void)n_models; (void)batch; (void)paths; (void)grad_scores; (void)dlog_pi; (void)dlogA;
-  (void)dE; (void)workspace; (void)ws_bytes; (void)stream_;
-  return FV_EUNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream_);
+  fv_status s = check_common(models, n_models, batch);
+  if (s != FV_OK) return s;
+  if (n_models != 1 || models[0].trans != FV_TRANS_DENSE || models[0].emit != FV_EMIT_DENSE)
+    return FV_EUNSUPPORTED;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1))) return FV_EINVAL;
+  if (batch->n_seq > 0 && (!paths || !grad_scores || !dlog_pi || !dlogA || !dE)) return FV_EINVAL;
+  if (ws_bytes < fv_backward_workspace_size(models, n_models, batch)) return FV_ENOMEM;
+  if (!batch->T_host) return FV_EINVAL;  // grid sizing uses the longest sequence
+  const int32_t n = batch->n_seq, K = models[0].K;
+  if (n == 0) return FV_OK;
+  int32_t max_T = 1;
+  for (int i = 0; i < n; ++i) max_T = std::max(max_T, batch->T_host[i]);
+  char* ws = static_cast<char*>(workspace);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  Job* jobs = reinterpret_cast<Job*>(ws + align_up(sizeof(WsHeader)));
+  PrepArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.T = batch->T;
+  pa.model_idx = batch->model_idx;
+  pa.e_off = batch->e_off;
+  pa.path_off = batch->path_off;
+  pa.n_seq = n;
+  pa.n_models = 1;
+  pa.mk.K[0] = K;
+  pa.aux_kind = 0;
+  pa.jobs = jobs;
+  pa.hdr = hdr;
+  pa.aux_cap = 0;
+  if (launch_prep(pa, st) != cudaSuccess) return FV_ECUDA;
+  if (launch_backward(jobs, n, K, paths, grad_scores, dlog_pi, dlogA, dE, max_T, hdr, st) != cudaSuccess)
+    return FV_ECUDA;
+  return FV_OK;
 }
 
 fv_status fv_timing_enable(int32_t on) {

@@ -153,6 +153,12 @@ cudaError_t launch_beam_resolve(const Job* jobs, const int32_t* order, int32_t b
                                 int32_t Wcap, int32_t pe_cap, int64_t div_stride, const int32_t* div_id,
                                 const float* div_val, const int32_t* div_mid, const int32_t* div_n, int32_t* paths,
                                 float* sval, WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_backward(const Job* jobs, int32_t n_seq, int32_t K, const int32_t* paths, const float* g,
+                            float* dlog_pi, float* dlogA, float* dE, int32_t max_T, const WsHeader* hdr,
+                            cudaStream_t st);
+cudaError_t launch_path_score_direct(const ScoreArgs& a, int32_t model, int32_t n_seq, const int32_t* T,
+                                     const int32_t* model_idx, const int64_t* e_off, const int64_t* path_off,
+                                     const int32_t* paths, float* scores, cudaStream_t st);
 cudaError_t launch_path_score(const ScoreArgs& a, const Job* jobs, const int32_t* order, int32_t begin,
                               int32_t count, const int32_t* paths, float* scores, const WsHeader* hdr,
                               cudaStream_t st);
