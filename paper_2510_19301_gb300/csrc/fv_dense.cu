@@ -159,9 +159,41 @@ struct Slot {
   int32_t tmid;               // sub: midpoint of the segment
   int32_t f_mid;              // this tick: 0 no MidState, 1 MidState = psi, 2 MidState = MidState_prev[psi]
   int32_t f_snap, f_map, f_k; // this tick: snapshot delta / store ancestor map / division index
-  int32_t pad;
+  int32_t sym;                // this tick: observation symbol (discrete emissions)
+  const float* erow;          // this tick: emission row E_t (dense emissions)
   PJob cur, pend;
 };
+
+// What every thread needs to know about a slot during one tick, written by
+// the slot's owner thread in the prologue and read with vector loads.
+struct __align__(16) TickDesc {
+  int32_t mode;       // 0 idle, 1 first step of the job (init), 2 max-plus step
+  int32_t f_mid;      // 0 none, 1 MidState = psi, 2 MidState = MidState_prev[psi]
+  int32_t f_snap;     // 1: root snapshot to global / sub snapshot to shared
+  int32_t q_prev;     // pruned start: q*_{m-1} (0 when m == 0)
+  float s_prev;       // pruned start: retained offset
+  int32_t first;      // 1 when t == 0 (start from pi)
+  int64_t psi_row;    // vanilla: element offset of psi_t[0]
+  const float* erow;  // dense emissions: E_t row
+  int64_t snap_row;   // root: element offset of the snapshot row (f_snap)
+  int64_t map_row;    // root: element offset of the map row, -1 if none
+  int32_t sym;        // discrete emissions: observation symbol x_t
+  int32_t pad[3];
+};
+
+// c = (d.lo + a.lo, d.hi + a.hi), two FP32 adds rounded to nearest even,
+// then acc = max(acc, c.lo, c.hi) with the 3-input max.
+__device__ __forceinline__ void fadd2_max3(float& acc, unsigned long long d, unsigned long long a) {
+  asm("{\n\t.reg .b64 c;\n\t.reg .f32 lo, hi;\n\tadd.rn.f32x2 c, %1, %2;\n\tmov.b64 {lo, hi}, c;\n\t"
+      "max.f32 %0, %0, lo, hi;\n\t}"
+      : "+f"(acc)
+      : "l"(d), "l"(a));
+}
+__device__ __forceinline__ void fadd2(unsigned long long d, unsigned long long a, float& c0, float& c1) {
+  unsigned long long c;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(c) : "l"(d), "l"(a));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(c0), "=f"(c1) : "l"(c));
+}
 
 __host__ __device__ inline int32_t flash_pe(int32_t T, int32_t P) {
   if (T <= 1) return 1;
@@ -173,54 +205,68 @@ __host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
   return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
 }
 
-template <int J, int S, int NW, int CL>
+template <int J, int S, int NW, int CL, int KPM>
 struct DenseCfg {
   static constexpr int NT = NW * 32;
   static constexpr int LJ = J / 8;
   static constexpr int LS = 32 / LJ;
   static constexpr int OPT = S * J / NT;
+  static constexpr int KP = KPM;          // rows, padded (-inf) to a fixed count
+  static constexpr int C = KPM / NW;      // rows per warp (one argmax chunk)
+  static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
   static_assert(LJ * LS == 32 && LS * 4 == S, "lane tile is 4 sequences x 8 columns");
-  static_assert((S * J) % NT == 0, "epilogue outputs per thread");
-  static size_t smem_bytes(int KP) {
-    const int KPS = KP + KP / 32;
-    return sizeof(float) * ((size_t)KP * J + 2ull * KP * S + 2ull * S * KPS + (size_t)NW * S * J +
-                            (size_t)S * KP) +
-           sizeof(uint16_t) * 2ull * S * KP;
-  }
+  static_assert((S * J) % NT == 0 && NT % J == 0, "epilogue: one column per thread, OPT slots");
+  static_assert(C % 4 == 0 && (32 % C == 0 || C % 32 == 0), "a chunk stays inside one skew block");
+  static constexpr size_t smem_bytes =
+      sizeof(float) * ((size_t)KP * J + 2ull * S * KPS + (size_t)NW * S * J + (size_t)S * KP) +
+      sizeof(uint16_t) * 2ull * S * KP;
 };
 
-template <int J, int S, int NW, int CL>
-__global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
-  using Cfg = DenseCfg<J, S, NW, CL>;
-  constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT;
+template <int J, int S, int NW, int CL, int KPM>
+__global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
+  using Cfg = DenseCfg<J, S, NW, CL, KPM>;
+  constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT, KP = Cfg::KP, C = Cfg::C, KPS = Cfg::KPS;
   extern __shared__ __align__(16) float smem[];
   __shared__ Slot slots[S];
+  __shared__ TickDesc tdesc[S];
 
-  const int K = a.K, KP = a.KP, C = KP / NW, KPS = KP + KP / 32;
-  float* sA = smem;                  // [KP][J]     logA column slab
-  float* sD = sA + (size_t)KP * J;   // [2][KP][S]  delta, row-major in i
-  float* sR = sD + 2 * KP * S;       // [2][S][KPS] delta per slot, bank-skewed
-  float* sPart = sR + 2 * S * KPS;   // [NW][S][J]  per-warp partial maxima
-  float* sSnap = sPart + NW * S * J; // [S][KP]     sub: delta at t_mid
+  const int K = a.K;
+  // logA column slab as row pairs: sA2[i/2][jj] = (A[i][j0+jj], A[i+1][j0+jj])
+  float* sA = smem;                   // [KP/2][J] float2
+  float* sD = sA + KP * J;            // [2][S][KPS] delta per slot, skewed rows
+  float* sPart = sD + 2 * S * KPS;    // [NW][S][J]  per-warp partial maxima
+  float* sSnap = sPart + NW * S * J;  // [S][KP]     sub: delta at t_mid
   uint16_t* sMid = reinterpret_cast<uint16_t*>(sSnap + S * KP);  // [2][S][KP] MidState
+  const float2* sA2 = reinterpret_cast<const float2*>(sA);
 
   const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
   const int j0 = (int)rank * J;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kind = a.kind;
+  // epilogue mapping: this thread owns column jj for slots s0 + r * (NT / J)
+  const int jj = tid % J, jcol = j0 + jj, s0 = tid / J;
+  constexpr int SSTEP = NT / J;
 
   if (a.hdr->status != 0) return;  // an earlier kernel recorded an error: do nothing
 
   for (int x = tid; x < KP * J; x += NT) {
-    const int i = x / J, j = j0 + x % J;
+    const int ip = x / (2 * J), c = (x / 2) % J, i = 2 * ip + (x & 1), j = j0 + c;
     sA[x] = (i < K && j < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
   }
-  for (int x = tid; x < 2 * KP * S + 2 * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
+  for (int x = tid; x < 2 * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
   for (int x = tid; x < 2 * S * KP; x += NT) sMid[x] = 0;
   if (tid < S) {
     slots[tid].state = kNeedPop;
     slots[tid].term = 0;
     slots[tid].pend.valid = 0;
+  }
+  // distributed shared memory bases of the peers (byte addresses)
+  uint32_t pD[CL], pMid[CL], pSnap[CL];
+#pragma unroll
+  for (int rr = 0; rr < CL; ++rr) {
+    pD[rr] = CL > 1 ? dsmem_addr(sD, rr) : 0u;
+    pMid[rr] = CL > 1 ? dsmem_addr(sMid, rr) : 0u;
+    pSnap[rr] = CL > 1 ? dsmem_addr(sSnap, rr) : 0u;
   }
   if (CL > 1) cluster_sync_all(); else __syncthreads();
 
@@ -298,21 +344,38 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
         }
         sl.state = kWaiting;
       }
-      // per-tick flags of a running job
-      sl.f_mid = sl.f_snap = sl.f_map = sl.f_k = 0;
+      // this tick's descriptor of the slot
+      TickDesc td;
+      td.mode = 0;
+      td.f_mid = td.f_snap = td.q_prev = td.first = td.sym = 0;
+      td.pad[0] = td.pad[1] = td.pad[2] = 0;
+      td.s_prev = 0.f;
+      td.psi_row = 0;
+      td.erow = nullptr;
+      td.snap_row = 0;
+      td.map_row = -1;
       if (sl.state == kRun) {
         const int t = sl.t;
+        const PJob& jb = sl.cur;
+        td.mode = (t == jb.m) ? 1 : 2;
+        td.first = (t == 0);
+        td.q_prev = jb.q_prev;
+        td.s_prev = jb.s_prev;
+        td.psi_row = jb.aux_off + (int64_t)t * K;
+        if (a.emit == FV_EMIT_DENSE) td.erow = a.E + jb.e_off + (int64_t)t * K;
+        else td.sym = __ldg(a.obs + jb.e_off + t);
         if (kind == kJobRoot) {
           const int is_div = (t == sl.ediv);
-          if (sl.eprev >= 0) sl.f_mid = (t == sl.eprev + 1) ? 1 : 2;
-          sl.f_snap = is_div;
-          sl.f_map = is_div && sl.kdiv >= 1;
-          sl.f_k = sl.kdiv;
+          if (sl.eprev >= 0) td.f_mid = (t == sl.eprev + 1) ? 1 : 2;
+          td.f_snap = is_div;
+          td.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)sl.kdiv * K;
+          td.map_row = (is_div && sl.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(sl.kdiv - 1) * K : -1;
         } else if (kind == kJobSub) {
-          sl.f_mid = (t == sl.tmid + 1) ? 1 : (t > sl.tmid + 1 ? 2 : 0);
-          sl.f_snap = (t == sl.tmid);
+          td.f_mid = (t == sl.tmid + 1) ? 1 : (t > sl.tmid + 1 ? 2 : 0);
+          td.f_snap = (t == sl.tmid);
         }
       }
+      tdesc[tid] = td;
     }
     const int live = (tid < S) && (slots[tid].state != kDone || slots[tid].term);
     if (!__syncthreads_or(live)) break;
@@ -322,12 +385,13 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
       for (int s = warp; s < S; s += NW) {
         if (!slots[s].term) continue;
         const PJob& jb = slots[s].cur;
+        const float* dl = sD + (cur * S + s) * KPS;
         if (kind == kJobVanilla) {
           // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q]
           float bv = -CUDART_INF_F;
           int bi = 0x7fffffff;
           for (int j = lane; j < K; j += 32) {
-            const float v = sD[((size_t)cur * KP + j) * S + s];
+            const float v = dl[j + ((j >> 5) << 2)];
             if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
           }
           for (int o = 16; o > 0; o >>= 1) {
@@ -337,36 +401,38 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
           }
           if (lane == 0) {
             a.qlast[jb.b] = bi;
-            a.scores[jb.b] = sD[((size_t)cur * KP + bi) * S + s];
+            a.scores[jb.b] = dl[bi + ((bi >> 5) << 2)];
           }
         } else if (kind == kJobSub && lane == 0) {
           // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
           const int tmid = (jb.m + jb.n) / 2;
-          int q = sMid[((size_t)cur * S + s) * KP + ((unsigned)jb.q_n < (unsigned)K ? jb.q_n : 0)];
+          int q = sMid[(cur * S + s) * KP + ((unsigned)jb.q_n < (unsigned)K ? jb.q_n : 0)];
           q = (unsigned)q < (unsigned)K ? q : 0;
           a.paths[jb.path_off + tmid] = q;
-          a.sval[jb.aux_off + tmid] = sSnap[(size_t)s * KP + q];
+          a.sval[jb.aux_off + tmid] = sSnap[s * KP + q];
         }
       }
     }
 
-    // ---- prefetch emission scores for this thread's epilogue outputs
+    // ---- prefetch this thread's emission scores (column jcol, OPT slots)
     float ev[OPT], pv[OPT];
+    TickDesc tdr[OPT];
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) tdr[r] = tdesc[s0 + r * SSTEP];
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
-      const int o = tid + r * NT, s = o / J, j = j0 + o % J;
       ev[r] = 0.f;
       pv[r] = 0.f;
-      const Slot& sl = slots[s];
-      if (sl.state == kRun && j < K) {
-        const int t = sl.t;
-        if (a.emit == FV_EMIT_DENSE) ev[r] = __ldg(a.E + sl.cur.e_off + (int64_t)t * K + j);
-        else ev[r] = __ldg(a.logB + (int64_t)j * a.V + __ldg(a.obs + sl.cur.e_off + t));
-        if (t == 0) pv[r] = __ldg(a.log_pi + j);
+      if (tdr[r].mode && jcol < K) {
+        ev[r] = a.emit == FV_EMIT_DENSE ? __ldg(tdr[r].erow + jcol) : __ldg(a.logB + (int64_t)jcol * a.V + tdr[r].sym);
+        if (tdr[r].first) pv[r] = __ldg(a.log_pi + jcol);
       }
     }
 
-    // ---- main loop: value-only tropical product over this warp's rows
+    // ---- main loop: value-only tropical product over this warp's C rows.
+    // Per 4 rows a lane loads delta[4 slots][4 rows] and logA[4 rows][8
+    // columns] as row pairs and issues one add.f32x2 + one 3-input max per
+    // 2 cells.
     {
       const int sg = lane / LJ, jg = lane % LJ;
       float acc[4][8];
@@ -374,100 +440,176 @@ __global__ void __launch_bounds__(NW * 32) dense_fwd_kernel(DenseArgs a) {
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 8; ++y) acc[x][y] = -CUDART_INF_F;
-      const float* dp = sD + (size_t)cur * KP * S + sg * 4;
-      const float* ap0 = sA + 4 * jg;
-      const float* ap1 = sA + 4 * LJ + 4 * jg;
-      const int i0 = warp * C, i1 = i0 + C;
-#pragma unroll 2
-      for (int i = i0; i < i1; ++i) {
-        const float4 d = *reinterpret_cast<const float4*>(dp + (size_t)i * S);
-        const float4 x0 = *reinterpret_cast<const float4*>(ap0 + (size_t)i * J);
-        const float4 x1 = *reinterpret_cast<const float4*>(ap1 + (size_t)i * J);
-        const float dv[4] = {d.x, d.y, d.z, d.w};
-        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const int i0 = warp * C;
+      const float* dbase = sD + (cur * S + sg * 4) * KPS + i0 + ((i0 >> 5) << 2);
+      const float2* abase = sA2 + (i0 / 2) * J + 2 * jg;
+#pragma unroll
+      for (int ii = 0; ii < C; ii += 4) {
+        ulonglong2 dq[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) dq[x] = *reinterpret_cast<const ulonglong2*>(dbase + x * KPS + ii);
+        ulonglong2 aq[2][4];
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + (ii / 2 + pr) * J + 2 * LJ * g);
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = fmaxf(acc[x][y], __fadd_rn(dv[x], xv[y]));
+          for (int g = 0; g < 4; ++g) {
+            fadd2_max3(acc[x][2 * g], dq[x].x, aq[0][g].x);
+            fadd2_max3(acc[x][2 * g], dq[x].y, aq[1][g].x);
+            fadd2_max3(acc[x][2 * g + 1], dq[x].x, aq[0][g].y);
+            fadd2_max3(acc[x][2 * g + 1], dq[x].y, aq[1][g].y);
+          }
       }
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        float* pp = sPart + ((size_t)warp * S + sg * 4 + x) * J;
-        *reinterpret_cast<float4*>(pp + 4 * jg) = make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
-        *reinterpret_cast<float4*>(pp + 4 * LJ + 4 * jg) = make_float4(acc[x][4], acc[x][5], acc[x][6], acc[x][7]);
+        float* pp = sPart + (warp * S + sg * 4 + x) * J + 2 * jg;
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          *reinterpret_cast<float2*>(pp + 2 * LJ * g) = make_float2(acc[x][2 * g], acc[x][2 * g + 1]);
       }
     }
     __syncthreads();
 
-    // ---- merge, exact argmax re-scan, + E, per-kind bookkeeping, broadcast
+    // ---- merge: per output, the first warp whose partial is the maximum
     const int nxt = cur ^ 1;
+    float best[OPT], val[OPT];
+    int wbase[OPT], arg[OPT];
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
-      const int o = tid + r * NT, s = o / J, jj = o % J, j = j0 + jj;
-      const Slot& sl = slots[s];
-      if (sl.state != kRun || j >= K) continue;
-      const PJob& jb = sl.cur;
-      float dval;
-      int arg = 0;
-      if (sl.t == jb.m) {
-        if (jb.m == 0) {
-          dval = __fadd_rn(pv[r], ev[r]);
-        } else {
-          // pruned start (Sec. V-B.2): only transitions out of q*_{m-1}
-          const float av = sA[(size_t)jb.q_prev * J + jj];
-          dval = a.complete ? __fadd_rn(av, ev[r]) : __fadd_rn(__fadd_rn(jb.s_prev, av), ev[r]);
-        }
-      } else {
-        float best = sPart[(size_t)s * J + jj];
-        int wb = 0;
-        for (int w = 1; w < NW; ++w) {
-          const float v = sPart[((size_t)w * S + s) * J + jj];
-          if (v > best) { best = v; wb = w; }
-        }
-        const float* dr = sR + ((size_t)cur * S + s) * KPS;
-        arg = wb * C;
-        float val = best;
-        for (int k = C - 1; k >= 0; --k) {
-          const int i = wb * C + k;
-          const float c = __fadd_rn(dr[i + (i >> 5)], sA[(size_t)i * J + jj]);
-          if (c == best) { arg = i; val = c; }
-        }
-        arg = arg < K ? arg : 0;  // only NaN inputs (unsupported) could leave it on a padded row
-        if (kind == kJobVanilla) a.psi[jb.aux_off + (int64_t)sl.t * K + j] = (uint16_t)arg;
-        dval = __fadd_rn(val, ev[r]);
-      }
-      if (sl.f_mid) {
-        const uint16_t mnew = sl.f_mid == 1 ? (uint16_t)arg : sMid[((size_t)cur * S + s) * KP + arg];
-        uint16_t* mp = sMid + ((size_t)nxt * S + s) * KP + j;
-        *mp = mnew;
-        for (int rr = 0; rr < CL; ++rr)
-          if (rr != (int)rank) dsmem_st_u16(dsmem_addr(mp, rr), mnew);
-        if (sl.f_map) a.maps[(int64_t)jb.b * a.map_stride + (int64_t)(sl.f_k - 1) * K + j] = mnew;
-      }
-      if (sl.f_snap) {
-        if (kind == kJobRoot) {
-          a.snaps[(int64_t)jb.b * a.snap_stride + (int64_t)sl.f_k * K + j] = dval;
-        } else {
-          float* sp = sSnap + (size_t)s * KP + j;
-          *sp = dval;
-          for (int rr = 0; rr < CL; ++rr)
-            if (rr != (int)rank) dsmem_st_f32(dsmem_addr(sp, rr), dval);
-        }
-      }
-      float* d1 = sD + ((size_t)nxt * KP + j) * S + s;
-      float* d2 = sR + ((size_t)nxt * S + s) * KPS + j + (j >> 5);
-      *d1 = dval;
-      *d2 = dval;
-      if (CL > 1) {
+      const int s = s0 + r * SSTEP;
+      const float* pp = sPart + s * J + jj;
+      float bv = pp[0];
+      int wb = 0;
 #pragma unroll
-        for (int rr = 0; rr < CL; ++rr) {
-          if (rr == (int)rank) continue;
-          dsmem_st_f32(dsmem_addr(d1, rr), dval);
-          dsmem_st_f32(dsmem_addr(d2, rr), dval);
+      for (int w = 1; w < NW; ++w) {
+        const float v = pp[w * S * J];
+        if (v > bv) { bv = v; wb = w; }
+      }
+      best[r] = bv;
+      val[r] = bv;
+      wbase[r] = wb * C;
+      arg[r] = wb * C;
+    }
+    // ---- exact argmax: rows of the winning chunk, descending, so the last
+    // match is the lowest row; the kept value is the recomputed candidate
+    {
+      const float* dr[OPT];
+      const float2* ar[OPT];
+#pragma unroll
+      for (int r = 0; r < OPT; ++r) {
+        const int s = s0 + r * SSTEP;
+        dr[r] = sD + (cur * S + s) * KPS + wbase[r] + ((wbase[r] >> 5) << 2);
+        ar[r] = sA2 + (wbase[r] / 2) * J + jj;
+      }
+#pragma unroll
+      for (int k = C / 2 - 1; k >= 0; --k) {
+#pragma unroll
+        for (int r = 0; r < OPT; ++r) {
+          float c0, c1;
+          fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k),
+                *reinterpret_cast<const unsigned long long*>(ar[r] + k * J), c0, c1);
+          if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
+          if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
         }
       }
     }
-    if (CL > 1) cluster_sync_all(); else __syncthreads();
+
+    // ---- + E, per-kind bookkeeping, broadcast delta_t.  Global stores
+    // (psi, root maps and snapshots) are kept in registers and issued after
+    // the cluster barrier's arrive, so its release only waits for the
+    // distributed shared memory writes.
+    int st_arg[OPT], st_mid[OPT];
+    float st_val[OPT];
+    int64_t st_off[OPT], st_moff[OPT];
+    uint32_t st_mask = 0;  // bit 2r: psi store, bit 2r+1: root snapshot (+ map)
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) {
+      const int s = s0 + r * SSTEP;
+      const TickDesc& td = tdr[r];
+      st_arg[r] = 0;
+      st_mid[r] = 0;
+      st_val[r] = 0.f;
+      st_off[r] = 0;
+      st_moff[r] = -1;
+      if (!td.mode || jcol >= K) continue;
+      float dval;
+      int ag = 0;
+      if (td.mode == 1) {
+        if (td.first) {
+          dval = __fadd_rn(pv[r], ev[r]);
+        } else {
+          // pruned start (Sec. V-B.2): only transitions out of q*_{m-1}
+          const float av = sA[((td.q_prev >> 1) * J + jj) * 2 + (td.q_prev & 1)];
+          dval = a.complete ? __fadd_rn(av, ev[r]) : __fadd_rn(__fadd_rn(td.s_prev, av), ev[r]);
+        }
+      } else {
+        ag = arg[r] < K ? arg[r] : 0;  // only NaN inputs (unsupported) could leave it on a padded row
+        if (kind == kJobVanilla) {
+          st_mask |= 1u << (2 * r);
+          st_arg[r] = ag;
+          st_off[r] = td.psi_row + jcol;
+        }
+        dval = __fadd_rn(val[r], ev[r]);
+      }
+      if (td.f_mid) {
+        const uint16_t mnew = td.f_mid == 1 ? (uint16_t)ag : sMid[(cur * S + s) * KP + ag];
+        const int mo = (nxt * S + s) * KP + jcol;
+        sMid[mo] = mnew;
+#pragma unroll
+        for (int rr = 0; rr < CL; ++rr)
+          if (rr != (int)rank) dsmem_st_u16(pMid[rr] + 2u * mo, mnew);
+        st_mid[r] = mnew;
+      }
+      if (td.f_snap) {
+        if (kind == kJobRoot) {
+          st_mask |= 1u << (2 * r + 1);
+          st_val[r] = dval;
+          st_off[r] = td.snap_row + jcol;
+          st_moff[r] = td.map_row >= 0 ? td.map_row + jcol : -1;
+        } else {
+          const int so = s * KP + jcol;
+          sSnap[so] = dval;
+#pragma unroll
+          for (int rr = 0; rr < CL; ++rr)
+            if (rr != (int)rank) dsmem_st_f32(pSnap[rr] + 4u * so, dval);
+        }
+      }
+      sD[(nxt * S + s) * KPS + jcol + ((jcol >> 5) << 2)] = dval;
+    }
+    // delta_t to the peers: the warp's 32 columns x OPT slots, re-read as
+    // 16-byte rows of 4 columns so each lane sends one vector per slot group
+    if (CL > 1) {
+      __syncwarp();
+      constexpr int LPS = 8;  // lanes per slot: 8 x 4 columns = the warp's 32 columns
+      const int wcol = j0 + (tid % J) - lane;  // first column of this warp
+#pragma unroll
+      for (int r0 = 0; r0 < OPT; r0 += 32 / LPS) {
+        const int r = r0 + lane / LPS;
+        if (r >= OPT) break;
+        const int s = s0 + r * SSTEP;
+        if (!tdesc[s].mode) continue;
+        const int c4 = wcol + 4 * (lane % LPS);
+        const int dof = (nxt * S + s) * KPS + c4 + ((c4 >> 5) << 2);
+        const float4 v = *reinterpret_cast<const float4*>(sD + dof);
+#pragma unroll
+        for (int rr = 0; rr < CL; ++rr)
+          if (rr != (int)rank) dsmem_st_v4f32(pD[rr] + 4u * dof, v.x, v.y, v.z, v.w);
+      }
+    }
+    if (CL > 1) cluster_arrive_release(); else __syncthreads();
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) {
+      if (st_mask & (1u << (2 * r))) a.psi[st_off[r]] = (uint16_t)st_arg[r];
+      if (st_mask & (1u << (2 * r + 1))) {
+        a.snaps[st_off[r]] = st_val[r];
+        if (st_moff[r] >= 0) a.maps[st_moff[r]] = (uint16_t)st_mid[r];
+      }
+    }
+    if (CL > 1) cluster_wait_acquire();
     if (tid < S && slots[tid].state == kRun) {
       Slot& sl = slots[tid];
       if (kind == kJobRoot && sl.t == sl.ediv) {
@@ -575,11 +717,12 @@ __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* o
 }
 
 // ------------------------------------------------------------ host launchers
-template <int J, int S, int NW, int CL>
-static cudaError_t launch_dense_cfg(const DenseArgs& a, int max_clusters, cudaStream_t st) {
-  using Cfg = DenseCfg<J, S, NW, CL>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL>;
-  const size_t smem = Cfg::smem_bytes(a.KP);
+template <int J, int S, int NW, int CL, int KPM>
+static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t st) {
+  using Cfg = DenseCfg<J, S, NW, CL, KPM>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM>;
+  a.KP = KPM;
+  const size_t smem = Cfg::smem_bytes;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0;
@@ -620,13 +763,9 @@ int dense_supported_K(int K) { return K >= 1 && K <= 256; }
 
 // Rows padded to a multiple of 4 * NW for the chosen configuration.
 cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st) {
-  if (a.K <= 64) {
-    a.KP = (a.K + 15) / 16 * 16;
-    return launch_dense_cfg<64, 16, 4, 1>(a, max_clusters, st);
-  }
-  a.KP = (a.K + 31) / 32 * 32;
-  if (a.K <= 128) return launch_dense_cfg<128, 8, 8, 1>(a, max_clusters, st);
-  return launch_dense_cfg<128, 8, 8, 2>(a, max_clusters, st);
+  if (a.K <= 64) return launch_dense_cfg<64, 16, 4, 1, 64>(a, max_clusters, st);
+  if (a.K <= 128) return launch_dense_cfg<128, 8, 8, 1, 128>(a, max_clusters, st);
+  return launch_dense_cfg<128, 8, 8, 2, 256>(a, max_clusters, st);
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t st) {
