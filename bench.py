@@ -134,6 +134,54 @@ def cpu_baseline(wl, seconds_target=20.0):
                       f"{cores} threads, {dt:.2f} s wall"}
 
 
+def time_decoder(dec, steps, warmup, lib):
+    """Device time per step (CUDA events on the launching stream) and the
+    mean duration of the library's main decode kernels per step."""
+    import ctypes
+
+    import torch
+    for _ in range(warmup):
+        dec.launch()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lib.fv_timing_enable(1)
+    e0.record(st)
+    for _ in range(steps):
+        dec.launch()
+    e1.record(st)
+    torch.cuda.synchronize()
+    tot, npairs = ctypes.c_float(0), ctypes.c_int32(0)
+    lib.fv_timing_read(ctypes.byref(tot), ctypes.byref(npairs))
+    lib.fv_timing_enable(0)
+    return e0.elapsed_time(e1) / steps, tot.value / max(steps, 1)
+
+
+def per_sequence_comparator(fv, m, lengths, E, K, n_sample, device):
+    """Plain GPU Viterbi: the same exact decoder launched once per sequence
+    (one sequence per call, one stream), timed on a sample of sequences."""
+    import torch
+    e_off = np.concatenate([[0], np.cumsum(lengths.astype(np.int64) * K)])
+    decs = []
+    for i in range(n_sample):
+        Ei = E.view(-1)[e_off[i]:e_off[i + 1]]
+        decs.append(fv.Decoder([m], fv.Batch([int(lengths[i])], E=Ei, models=[m], device=device)))
+    for d in decs:
+        d.launch()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for d in decs:
+        d.launch()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps = int(lengths[:n_sample].astype(np.int64).sum()) * K
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "sample": f"first {n_sample} sequences, one launch each",
+            "ms": ms}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -252,6 +300,23 @@ def run_ours(args):
     h2d = E_host.numel() * 4
     d2h = P_host.numel() * 4 + S_host.numel() * 4
 
+    modes = {}
+    if not args.quick:
+        for P in (4, 16, 64):
+            dflash = fv.Decoder([m], batch, mode="flash", P=P)
+            dflash(check=True)
+            fms, fk = time_decoder(dflash, max(2, args.steps // 20), 2, lib)
+            modes[f"flash_P{P}"] = {"value": state_steps / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                                   "time_vs_vanilla": fms / ms, "bit_identical_to_vanilla": None}
+            pv_, sv_ = dec.paths.clone(), dec.scores.clone()
+            pf_, sf_ = dflash.paths, dflash.scores
+            modes[f"flash_P{P}"]["bit_identical_to_vanilla"] = bool(
+                torch.equal(pv_, pf_) and torch.equal(sv_.view(torch.int32), sf_.view(torch.int32)))
+            del dflash
+        comp = per_sequence_comparator(fv, m, lengths, wl["E"], K, 32, device)
+        comp["batched_over_per_sequence"] = value / world / comp["value"]
+        modes["plain_per_sequence_gpu"] = comp
+
     pk, pk_kind = peaks()
     sm_mhz = clocks["sm_mhz"] or pk.get("sm_max_mhz", 2070.0)
     peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
@@ -273,6 +338,8 @@ def run_ours(args):
                         "ops_per_cell": 2, "cells_per_launch": cells, "kernel_ms": fwd_ms},
            "e2e": {"value": world * state_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
+    if modes:
+        out["modes"] = modes
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -293,6 +360,7 @@ def main():
     ap.add_argument("--budget", type=int, default=0)
     ap.add_argument("--n-seq", dest="n_seq", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the FLASH and per-sequence rows")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
