@@ -104,8 +104,8 @@ def make_workload(args, rank, device):
 
     import paper_2510_19301_gb300 as fv
     import workloads as W
-    K = 256
-    log_pi, logA = W.config2_model(seed=2)
+    K = args.K
+    log_pi, logA = W.config2_model(seed=2, K=K)
     lengths = W.config2_lengths(seed=2 + 7919 * rank, n_seq=args.n_seq)
     E = W.gaussian_emissions_packed_device(int(lengths.sum()), K, seed=2 + 7919 * rank, device=device)
     m = fv.Model(log_pi, logA, device=device)
@@ -323,10 +323,12 @@ def run_ours(args):
     achieved = 2.0 * cells / (fwd_ms / 1e3) / 1e12
     launches = args.steps * 4
 
+    wl_name = WORKLOAD if (args.K == 256 and args.n_seq == 1024) else WORKLOAD.replace(
+        "1024 seqs, K=256", f"{args.n_seq} seqs, K={args.K}")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "mode": args.mode, "P": args.P, "B": args.B,
+           "config": {"workload": wl_name, "mode": args.mode, "P": args.P, "B": args.B,
                       "n_seq": int(len(lengths)), "sum_T": int(lengths.sum()), "K": K,
                       "l2": "inputs larger than L2 (E is %.2f GB per step)" % (wl["E"].numel() * 4 / 1e9)},
            "clocks": clocks,
@@ -359,6 +361,7 @@ def main():
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--budget", type=int, default=0)
     ap.add_argument("--n-seq", dest="n_seq", type=int, default=1024)
+    ap.add_argument("--K", type=int, default=256, help="states (the default workload has K=256)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FLASH and per-sequence rows")
     args = ap.parse_args()

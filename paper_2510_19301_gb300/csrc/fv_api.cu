@@ -100,6 +100,7 @@ FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b
 struct Layout {
   size_t hdr, jobs, order, qlast, aux, aux2, maps, snaps, listA, listB, pos, bsum, counts, total;
   size_t bscratch, div_id, div_val, div_mid, div_n;
+  size_t ap, snapx;  // streamed exact configurations (K > 256)
   uint64_t aux_elems;
   int64_t map_stride, snap_stride, list_cap;
   int32_t Wcap, Bcap, pe_cap, max_ctas;
@@ -160,6 +161,26 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
     L.maps = end;
     L.snaps = align_up(L.maps + sizeof(uint16_t) * (size_t)L.map_stride * n);
     end = align_up(L.snaps + sizeof(float) * (size_t)L.snap_stride * n);
+  }
+  if (mode != FV_BEAM) {
+    // row-pair copy of the largest streamed model's logA, reused per model,
+    // and the streamed sub-job snapshots of every possible cluster
+    size_t ap_bytes = 0;
+    int32_t kpm_max = 0;
+    for (int m = 0; m < n_models; ++m) {
+      int kpm = 0, cols = 0;
+      dense_stream_geometry(models[m].K, &kpm, &cols);
+      ap_bytes = std::max(ap_bytes, (size_t)(kpm / 2) * cols * 8);
+      kpm_max = std::max(kpm_max, kpm);
+    }
+    if (ap_bytes) {
+      int dev = 0, nsm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      L.ap = end;
+      L.snapx = align_up(L.ap + ap_bytes);
+      end = align_up(L.snapx + sizeof(float) * (size_t)(nsm / 4 + 1) * 8 * kpm_max);
+    }
   }
   if (mode == FV_BEAM) {
     L.Bcap = fp ? kmax : L.Wcap;  // FLASH-BS subtasks may be re-run with every state
@@ -464,6 +485,16 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
     da.P = p->P;
     da.complete = (p->flags & FV_COMPLETE_PRUNING) ? 1 : 0;
     da.hdr = hdr;
+    {
+      int kpm = 0, cols = 0;
+      dense_stream_geometry(md.K, &kpm, &cols);
+      if (kpm) {
+        da.Ap = reinterpret_cast<const float2*>(ws + L.ap);
+        da.ap_stride = cols;
+        da.snap_scratch = reinterpret_cast<float*>(ws + L.snapx);
+        if (launch_ap_prep(md.logA, md.K, reinterpret_cast<float2*>(ws + L.ap), st) != cudaSuccess) return FV_ECUDA;
+      }
+    }
     if (p->mode == FV_VANILLA) {
       uint16_t* psi = reinterpret_cast<uint16_t*>(ws + L.aux);
       da.kind = kJobVanilla;

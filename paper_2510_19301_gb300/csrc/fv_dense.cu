@@ -205,39 +205,52 @@ __host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
   return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
 }
 
-template <int J, int S, int NW, int CL, int KPM>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM>
 struct DenseCfg {
   static constexpr int NT = NW * 32;
   static constexpr int LJ = J / 8;
   static constexpr int LS = 32 / LJ;
   static constexpr int OPT = S * J / NT;
   static constexpr int KP = KPM;          // rows, padded (-inf) to a fixed count
-  static constexpr int C = KPM / NW;      // rows per warp (one argmax chunk)
+  static constexpr int C = KPM / NW;      // rows per warp
+  static constexpr int CH = STREAM ? 32 : C;  // rows per argmax chunk
+  static constexpr int NST = KPM <= 512 ? 8 : 5;  // streamed: ring stages of 4 rows per warp
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
   static_assert(LJ * LS == 32 && LS * 4 == S, "lane tile is 4 sequences x 8 columns");
   static_assert((S * J) % NT == 0 && NT % J == 0, "epilogue: one column per thread, OPT slots");
-  static_assert(C % 4 == 0 && (32 % C == 0 || C % 32 == 0), "a chunk stays inside one skew block");
+  static_assert(C % CH == 0 && CH % 4 == 0 && (32 % CH == 0 || CH % 32 == 0), "chunks inside skew blocks");
+  static_assert(!STREAM || C / CH <= 255 * 1, "chunk ids fit a byte");
+  // resident: logA slab [KP/2][J] float2; streamed: per-warp ring of NST
+  // stages x 2 row pairs x J float2, plus the chunk id of each partial
+  static constexpr size_t a_floats = STREAM ? (size_t)NW * NST * 4 * J : (size_t)KP * J;
+  static constexpr size_t snap_floats = STREAM ? 0 : (size_t)S * KP;
   static constexpr size_t smem_bytes =
-      sizeof(float) * ((size_t)KP * J + 2ull * S * KPS + (size_t)NW * S * J + (size_t)S * KP) +
-      sizeof(uint16_t) * 2ull * S * KP;
+      sizeof(float) * (a_floats + 2ull * S * KPS + (size_t)NW * S * J + snap_floats) +
+      sizeof(uint16_t) * 2ull * S * KP + (STREAM ? (size_t)NW * S * J : 0);
 };
 
-template <int J, int S, int NW, int CL, int KPM>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM>
 __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM>;
   constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT, KP = Cfg::KP, C = Cfg::C, KPS = Cfg::KPS;
+  constexpr int CH = Cfg::CH, NST = Cfg::NST;
   extern __shared__ __align__(16) float smem[];
   __shared__ Slot slots[S];
   __shared__ TickDesc tdesc[S];
 
   const int K = a.K;
-  // logA column slab as row pairs: sA2[i/2][jj] = (A[i][j0+jj], A[i+1][j0+jj])
-  float* sA = smem;                   // [KP/2][J] float2
-  float* sD = sA + KP * J;            // [2][S][KPS] delta per slot, skewed rows
-  float* sPart = sD + 2 * S * KPS;    // [NW][S][J]  per-warp partial maxima
-  float* sSnap = sPart + NW * S * J;  // [S][KP]     sub: delta at t_mid
-  uint16_t* sMid = reinterpret_cast<uint16_t*>(sSnap + S * KP);  // [2][S][KP] MidState
+  // resident: logA column slab as row pairs sA2[i/2][jj] = (A[i][j0+jj],
+  // A[i+1][j0+jj]); streamed: each warp's ring of row-pair stages, filled
+  // with cp.async from the row-pair copy a.Ap in global memory
+  float* sA = smem;                           // resident [KP/2][J] / streamed [NW][NST][2][J] float2
+  float* sD = sA + Cfg::a_floats;             // [2][S][KPS] delta per slot, skewed rows
+  float* sPart = sD + 2 * S * KPS;            // [NW][S][J]  per-warp partial maxima
+  float* sSnap = sPart + NW * S * J;          // resident [S][KP] sub: delta at t_mid
+  uint16_t* sMid = reinterpret_cast<uint16_t*>(sSnap + Cfg::snap_floats);  // [2][S][KP] MidState
+  uint8_t* sPC = reinterpret_cast<uint8_t*>(sMid + 2 * S * KP);            // streamed [NW][S][J] chunk
   const float2* sA2 = reinterpret_cast<const float2*>(sA);
+  // streamed: global snapshot rows of this cluster's slots (sub jobs)
+  float* gSnap = STREAM ? a.snap_scratch + (size_t)(blockIdx.x / CL) * S * KP : nullptr;
 
   const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
   const int j0 = (int)rank * J;
@@ -249,9 +262,11 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
 
   if (a.hdr->status != 0) return;  // an earlier kernel recorded an error: do nothing
 
-  for (int x = tid; x < KP * J; x += NT) {
-    const int ip = x / (2 * J), c = (x / 2) % J, i = 2 * ip + (x & 1), j = j0 + c;
-    sA[x] = (i < K && j < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
+  if constexpr (!STREAM) {
+    for (int x = tid; x < KP * J; x += NT) {
+      const int ip = x / (2 * J), c = (x / 2) % J, i = 2 * ip + (x & 1), j = j0 + c;
+      sA[x] = (i < K && j < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
+    }
   }
   for (int x = tid; x < 2 * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
   for (int x = tid; x < 2 * S * KP; x += NT) sMid[x] = 0;
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   for (int rr = 0; rr < CL; ++rr) {
     pD[rr] = CL > 1 ? dsmem_addr(sD, rr) : 0u;
     pMid[rr] = CL > 1 ? dsmem_addr(sMid, rr) : 0u;
-    pSnap[rr] = CL > 1 ? dsmem_addr(sSnap, rr) : 0u;
+    pSnap[rr] = (CL > 1 && !STREAM) ? dsmem_addr(sSnap, rr) : 0u;
   }
   if (CL > 1) cluster_sync_all(); else __syncthreads();
 
@@ -409,7 +424,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           int q = sMid[(cur * S + s) * KP + ((unsigned)jb.q_n < (unsigned)K ? jb.q_n : 0)];
           q = (unsigned)q < (unsigned)K ? q : 0;
           a.paths[jb.path_off + tmid] = q;
-          a.sval[jb.aux_off + tmid] = sSnap[s * KP + q];
+          a.sval[jb.aux_off + tmid] = STREAM ? gSnap[s * KP + q] : sSnap[s * KP + q];
         }
       }
     }
@@ -433,7 +448,90 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
     // Per 4 rows a lane loads delta[4 slots][4 rows] and logA[4 rows][8
     // columns] as row pairs and issues one add.f32x2 + one 3-input max per
     // 2 cells.
-    {
+    if constexpr (STREAM) {
+      // streamed: this warp's C rows of logA arrive 4 rows at a time through
+      // an NST-stage cp.async ring; chunk winners (first chunk of CH rows
+      // reaching the running maximum) are kept per output in registers
+      const int sg = lane / LJ, jg = lane % LJ;
+      float acc[4][8], bst[4][8];
+      int bch[4][8];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          acc[x][y] = -CUDART_INF_F;
+          bst[x][y] = -CUDART_INF_F;
+          bch[x][y] = 0;
+        }
+      const int i0 = warp * C;
+      float2* ring = reinterpret_cast<float2*>(sA) + warp * NST * 2 * J;
+      const float2* gsrc = a.Ap + (int64_t)(i0 / 2) * a.ap_stride + j0;
+      constexpr int NIT = C / 4;
+      auto issue = [&](int it) {
+        float2* dst = ring + (it % NST) * 2 * J;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = lane + 32 * u, pr = q / (J / 2), c2 = (q % (J / 2)) * 2;
+          cp_async16(dst + pr * J + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
+        }
+      };
+#pragma unroll
+      for (int k = 0; k < NST - 1; ++k) {
+        if (k < NIT) issue(k);
+        cp_async_commit();
+      }
+      const float* dbase0 = sD + (cur * S + sg * 4) * KPS;
+#pragma unroll 1
+      for (int it = 0; it < NIT; ++it) {
+        cp_async_wait<NST - 2>();
+        __syncwarp();
+        if (it + NST - 1 < NIT) issue(it + NST - 1);
+        cp_async_commit();
+        const int i = i0 + 4 * it;
+        const float* dbase = dbase0 + i + ((i >> 5) << 2);
+        const float2* abase = ring + (it % NST) * 2 * J + 2 * jg;
+        ulonglong2 dq[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) dq[x] = *reinterpret_cast<const ulonglong2*>(dbase + x * KPS);
+        ulonglong2 aq[2][4];
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + pr * J + 2 * LJ * g);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            fadd2_max3(acc[x][2 * g], dq[x].x, aq[0][g].x);
+            fadd2_max3(acc[x][2 * g], dq[x].y, aq[1][g].x);
+            fadd2_max3(acc[x][2 * g + 1], dq[x].x, aq[0][g].y);
+            fadd2_max3(acc[x][2 * g + 1], dq[x].y, aq[1][g].y);
+          }
+        if ((it + 1) % (CH / 4) == 0) {
+          const int c = warp * (C / CH) + it / (CH / 4);
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+              if (acc[x][y] > bst[x][y]) { bst[x][y] = acc[x][y]; bch[x][y] = c; }
+              acc[x][y] = -CUDART_INF_F;
+            }
+        }
+      }
+      cp_async_wait<0>();
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        float* pp = sPart + (warp * S + sg * 4 + x) * J + 2 * jg;
+        uint8_t* pc = sPC + (warp * S + sg * 4 + x) * J + 2 * jg;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          *reinterpret_cast<float2*>(pp + 2 * LJ * g) = make_float2(bst[x][2 * g], bst[x][2 * g + 1]);
+          pc[2 * LJ * g] = (uint8_t)bch[x][2 * g];
+          pc[2 * LJ * g + 1] = (uint8_t)bch[x][2 * g + 1];
+        }
+      }
+    } else     {
       const int sg = lane / LJ, jg = lane % LJ;
       float acc[4][8];
 #pragma unroll
@@ -484,36 +582,65 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       const float* pp = sPart + s * J + jj;
       float bv = pp[0];
       int wb = 0;
+      if constexpr (STREAM) {
+        const uint8_t* pc = sPC + s * J + jj;
+        wb = pc[0];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        const float v = pp[w * S * J];
-        if (v > bv) { bv = v; wb = w; }
+        for (int w = 1; w < NW; ++w) {
+          const float v = pp[w * S * J];
+          if (v > bv) { bv = v; wb = pc[w * S * J]; }
+        }
+      } else {
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {
+          const float v = pp[w * S * J];
+          if (v > bv) { bv = v; wb = w; }
+        }
       }
       best[r] = bv;
       val[r] = bv;
-      wbase[r] = wb * C;
-      arg[r] = wb * C;
+      wbase[r] = wb * CH;
+      arg[r] = wb * CH;
     }
     // ---- exact argmax: rows of the winning chunk, descending, so the last
     // match is the lowest row; the kept value is the recomputed candidate
     {
       const float* dr[OPT];
       const float2* ar[OPT];
+      const int64_t astr = STREAM ? a.ap_stride : J;
 #pragma unroll
       for (int r = 0; r < OPT; ++r) {
         const int s = s0 + r * SSTEP;
         dr[r] = sD + (cur * S + s) * KPS + wbase[r] + ((wbase[r] >> 5) << 2);
-        ar[r] = sA2 + (wbase[r] / 2) * J + jj;
+        ar[r] = STREAM ? a.Ap + (int64_t)(wbase[r] / 2) * a.ap_stride + jcol : sA2 + (wbase[r] / 2) * J + jj;
       }
-#pragma unroll
-      for (int k = C / 2 - 1; k >= 0; --k) {
+      if constexpr (STREAM) {
+        // streamed: the chunk's logA pairs come from L2; load one output's
+        // CH/2 pairs at once so their latencies overlap, then compare
 #pragma unroll
         for (int r = 0; r < OPT; ++r) {
-          float c0, c1;
-          fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k),
-                *reinterpret_cast<const unsigned long long*>(ar[r] + k * J), c0, c1);
-          if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
-          if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+          unsigned long long av[CH / 2];
+#pragma unroll
+          for (int k = 0; k < CH / 2; ++k) av[k] = __ldg(reinterpret_cast<const unsigned long long*>(ar[r] + k * astr));
+#pragma unroll
+          for (int k = CH / 2 - 1; k >= 0; --k) {
+            float c0, c1;
+            fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k), av[k], c0, c1);
+            if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
+            if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = CH / 2 - 1; k >= 0; --k) {
+#pragma unroll
+          for (int r = 0; r < OPT; ++r) {
+            float c0, c1;
+            fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k),
+                  *reinterpret_cast<const unsigned long long*>(ar[r] + k * astr), c0, c1);
+            if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
+            if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+          }
         }
       }
     }
@@ -543,7 +670,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           dval = __fadd_rn(pv[r], ev[r]);
         } else {
           // pruned start (Sec. V-B.2): only transitions out of q*_{m-1}
-          const float av = sA[((td.q_prev >> 1) * J + jj) * 2 + (td.q_prev & 1)];
+          const float av = STREAM ? __ldg(a.logA + (int64_t)td.q_prev * K + jcol)
+                                  : sA[((td.q_prev >> 1) * J + jj) * 2 + (td.q_prev & 1)];
           dval = a.complete ? __fadd_rn(av, ev[r]) : __fadd_rn(__fadd_rn(td.s_prev, av), ev[r]);
         }
       } else {
@@ -570,6 +698,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           st_val[r] = dval;
           st_off[r] = td.snap_row + jcol;
           st_moff[r] = td.map_row >= 0 ? td.map_row + jcol : -1;
+        } else if constexpr (STREAM) {
+          gSnap[s * KP + jcol] = dval;
         } else {
           const int so = s * KP + jcol;
           sSnap[so] = dval;
@@ -717,10 +847,10 @@ __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* o
 }
 
 // ------------------------------------------------------------ host launchers
-template <int J, int S, int NW, int CL, int KPM>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM>
 static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t st) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM>;
   a.KP = KPM;
   const size_t smem = Cfg::smem_bytes;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -759,13 +889,43 @@ static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-int dense_supported_K(int K) { return K >= 1 && K <= 256; }
+int dense_supported_K(int K) { return K >= 1 && K <= 1024; }
+
+// Streamed configurations (K > 256) read logA from a row-pair copy
+// Ap[i/2][c] = (A[i][c], A[i+1][c]), rows padded to the configuration's row
+// count and columns to cluster x 128, padding -inf.
+void dense_stream_geometry(int K, int* KPM, int* cols) {
+  if (K <= 256) { *KPM = 0; *cols = 0; return; }
+  if (K <= 512) { *KPM = 512; *cols = 512; return; }
+  *KPM = 1024;
+  *cols = 1024;
+}
+
+__global__ void ap_prep_kernel(const float* logA, int K, int KPM, int cols, float2* Ap) {
+  const int64_t n = (int64_t)(KPM / 2) * cols;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const int ip = (int)(x / cols), c = (int)(x % cols), i = 2 * ip;
+    const float lo = (i < K && c < K) ? logA[(int64_t)i * K + c] : -CUDART_INF_F;
+    const float hi = (i + 1 < K && c < K) ? logA[(int64_t)(i + 1) * K + c] : -CUDART_INF_F;
+    Ap[x] = make_float2(lo, hi);
+  }
+}
+
+cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st) {
+  int KPM, cols;
+  dense_stream_geometry(K, &KPM, &cols);
+  if (!KPM) return cudaSuccess;
+  ap_prep_kernel<<<1024, 256, 0, st>>>(logA, K, KPM, cols, Ap);
+  return cudaGetLastError();
+}
 
 // Rows padded to a multiple of 4 * NW for the chosen configuration.
 cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st) {
-  if (a.K <= 64) return launch_dense_cfg<64, 16, 4, 1, 64>(a, max_clusters, st);
-  if (a.K <= 128) return launch_dense_cfg<128, 8, 8, 1, 128>(a, max_clusters, st);
-  return launch_dense_cfg<128, 8, 8, 2, 256>(a, max_clusters, st);
+  if (a.K <= 64) return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
+  if (a.K <= 128) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
+  if (a.K <= 256) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
+  if (a.K <= 512) return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
+  return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t st) {

@@ -89,4 +89,15 @@ __device__ inline void dsmem_st_s64(uint32_t addr, long long v) {
 
 __device__ inline float ld_nc(const float* p) { return __ldg(p); }
 
+// 16-byte asynchronous global -> shared copy (bypasses L1), and its groups.
+__device__ inline void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace fv

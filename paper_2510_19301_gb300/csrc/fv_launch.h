@@ -65,6 +65,9 @@ struct DenseArgs {
   int64_t snap_stride;
   int32_t P;
   int32_t complete;           // offset-0 (complete pruning) start for subtasks
+  const float2* Ap;           // streamed configurations: row-pair copy of logA
+  int64_t ap_stride;          // float2 per row pair of Ap
+  float* snap_scratch;        // streamed configurations: sub snapshots [clusters][S][rows]
   WsHeader* hdr;
 };
 
@@ -122,6 +125,8 @@ struct ScoreArgs {
 };
 
 int dense_supported_K(int K);
+void dense_stream_geometry(int K, int* KPM, int* cols);
+cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st);
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t st);
 cudaError_t launch_order(const Job* jobs, int32_t n, int32_t nosort, int32_t* order, cudaStream_t st);
 cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st);

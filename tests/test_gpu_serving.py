@@ -1,0 +1,35 @@
+"""Serving loop on the GPU: requests of mixed K and T, exact and beam,
+arrive over time and overlap on the device; every result must equal the
+result of decoding that request alone (bit for bit), and latency
+percentiles are reported."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_results_in_the_mix_equal_results_alone():
+    import paper_2510_19301_gb300 as fv
+    from paper_2510_19301_gb300.serve import GpuBackend, Server, poisson_requests
+    fv._lib.load(build_if_missing=True)
+    reqs = poisson_requests(rate=2000.0, seconds=0.04, seed=11, Ks=(64, 256, 1024), tmin=20, tmax=600)
+    assert len(reqs) > 30
+    be = GpuBackend(n_streams=16, keep_results=True)
+    srv = Server(be, mem_budget_bytes=4 << 30, max_inflight=16)
+    rep = srv.run(reqs)
+    assert rep["failed"] == 0 and rep["requests"] == len(reqs)
+    assert rep["p99_ms"] >= rep["p50_ms"] > 0
+    overlapped = sum(1 for r in srv.done
+                     if r.admitted < max((o.finished for o in srv.done if o.rid < r.rid), default=-1.0))
+    assert overlapped > 0, "no request ran while another was on the GPU"
+    # alone: same seeded inputs, one request at a time on the default stream
+    for r in srv.done:
+        log_pi, logA, E = be.make_inputs(r)
+        m = fv.Model(log_pi, logA)
+        b = fv.Batch([r.T], E=E.view(-1), models=[m])
+        mode = {"exact": "vanilla", "beam": "beam"}[r.mode]
+        p, s = fv.decode([m], b, mode=mode, B=r.B if r.mode == "beam" else 0, P=0 if r.mode == "beam" else 1)
+        pm, sm = r.result
+        assert np.array_equal(p[:r.T].cpu().numpy(), pm), r
+        assert np.float32(s[0].item()).view(np.int32) == np.float32(sm).view(np.int32)
