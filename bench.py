@@ -182,6 +182,23 @@ def per_sequence_comparator(fv, m, lengths, E, K, n_sample, device):
             "ms": ms}
 
 
+def serving_run(seconds, rate=2000.0, n_streams=128, max_wall=30.0):
+    """Serving loop: Poisson arrivals, mixed K and T, exact and beam B=256,
+    admitted under a 40 GB device-memory budget.  Admission stops after
+    max_wall seconds; requests still waiting then are counted as not served
+    (an offered load above capacity shows up there and in the latencies)."""
+    from paper_2510_19301_gb300.serve import GpuBackend, Server, poisson_requests
+    reqs = poisson_requests(rate=rate, seconds=seconds, seed=6)
+    be = GpuBackend(n_streams=n_streams)
+    srv = Server(be, mem_budget_bytes=40 << 30, max_inflight=n_streams)
+    rep = srv.run(reqs, max_wall=max(max_wall, 3 * seconds))
+    rep.update({"arrival_rate_req_s": rate, "arrival_window_s": seconds, "offered": len(reqs),
+                "mix": "K uniform {64,256,1024}, T log-uniform [100,20000], 50% exact (vanilla) / "
+                       "50% beam B=256",
+                "streams": n_streams})
+    return rep
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -342,6 +359,8 @@ def run_ours(args):
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
     if modes:
         out["modes"] = modes
+    if rank == 0 and args.serve_seconds > 0:
+        out["serving"] = serving_run(args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -364,6 +383,8 @@ def main():
     ap.add_argument("--K", type=int, default=256, help="states (the default workload has K=256)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FLASH and per-sequence rows")
+    ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=2.0,
+                    help="arrival window of the serving run (60 = the full serving workload; 0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -64,6 +64,7 @@ class Server:
         self.failed: list[Request] = []
         self.bytes_in_use = 0
         self.peak_bytes = 0
+        self.not_served = 0
         self.t0 = None
 
     def now(self):
@@ -113,13 +114,22 @@ class Server:
             self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
             self.inflight.append((req, handle))
 
-    def run(self, requests, realtime: bool = True, idle_sleep: float = 0.0):
+    def run(self, requests, realtime: bool = True, idle_sleep: float = 0.0, max_wall: float = math.inf):
         """Replay requests at their arrival times (host clock) until all are
-        finished.  With realtime=False every request is available at once."""
+        finished.  With realtime=False every request is available at once.
+        After max_wall seconds no more requests are admitted; those still
+        waiting are reported as not served."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         self.t0 = self.clock()
         i = 0
         while i < len(reqs) or self.waiting or self.inflight:
+            if self.now() > max_wall:
+                self.not_served = len(self.waiting) + (len(reqs) - i)
+                self.waiting.clear()
+                i = len(reqs)
+                while self.inflight:
+                    self.step()
+                break
             now = self.now()
             while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
                 self.submit(reqs[i])
@@ -135,7 +145,7 @@ class Server:
         cells = sum(self.backend.cells(r) for r in self.done)
         steps = sum(r.T * r.K for r in self.done)
         return {
-            "requests": len(self.done), "failed": len(self.failed),
+            "requests": len(self.done), "failed": len(self.failed), "not_served": self.not_served,
             "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
             "mean_ms": float(lat.mean() * 1e3) if lat.size else None,

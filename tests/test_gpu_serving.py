@@ -28,6 +28,7 @@ def test_results_in_the_mix_equal_results_alone():
         log_pi, logA, E = be.make_inputs(r)
         m = fv.Model(log_pi, logA)
         b = fv.Batch([r.T], E=E.view(-1), models=[m])
+        # alone through the exact decoder (exact requests) or the same beam
         mode = {"exact": "vanilla", "beam": "beam"}[r.mode]
         p, s = fv.decode([m], b, mode=mode, B=r.B if r.mode == "beam" else 0, P=0 if r.mode == "beam" else 1)
         pm, sm = r.result
