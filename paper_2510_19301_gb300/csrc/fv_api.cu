@@ -101,6 +101,7 @@ struct Layout {
   size_t hdr, jobs, order, qlast, aux, aux2, maps, snaps, listA, listB, pos, bsum, counts, total;
   size_t bscratch, div_id, div_val, div_mid, div_n;
   size_t ap, snapx;  // streamed exact configurations (K > 256)
+  size_t wide;       // whole-GPU configuration scratch (K > 1024)
   uint64_t aux_elems;
   int64_t map_stride, snap_stride, list_cap;
   int32_t Wcap, Bcap, pe_cap, max_ctas;
@@ -174,12 +175,14 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
       kpm_max = std::max(kpm_max, kpm);
     }
     if (ap_bytes) {
-      int dev = 0, nsm = 1;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const int nsm = device_sm_count();
       L.ap = end;
       L.snapx = align_up(L.ap + ap_bytes);
       end = align_up(L.snapx + sizeof(float) * (size_t)(nsm / 4 + 1) * 8 * kpm_max);
+      if (kmax > 1024) {
+        L.wide = end;
+        end = align_up(L.wide + wide_scratch_bytes(kmax, nsm));
+      }
     }
   }
   if (mode == FV_BEAM) {
@@ -493,6 +496,18 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
         da.ap_stride = cols;
         da.snap_scratch = reinterpret_cast<float*>(ws + L.snapx);
         if (launch_ap_prep(md.logA, md.K, reinterpret_cast<float2*>(ws + L.ap), st) != cudaSuccess) return FV_ECUDA;
+      }
+      if (md.K > 1024) {
+        // whole-GPU engine scratch: the same carving as wide_scratch_bytes
+        const size_t lanes_k = (size_t)kWideLanes * md.K;
+        char* w = ws + L.wide;
+        da.wide_D = reinterpret_cast<float*>(w);
+        w += align_up(2 * sizeof(float) * lanes_k);
+        da.wide_M = reinterpret_cast<uint16_t*>(w);
+        w += align_up(2 * sizeof(uint16_t) * lanes_k);
+        da.wide_X = reinterpret_cast<float*>(w);
+        w += align_up(2 * sizeof(float) * lanes_k);
+        da.wide_flags = reinterpret_cast<uint32_t*>(w);
       }
     }
     if (p->mode == FV_VANILLA) {

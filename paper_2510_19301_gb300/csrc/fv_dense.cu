@@ -889,13 +889,33 @@ static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-int dense_supported_K(int K) { return K >= 1 && K <= 1024; }
+int device_sm_count() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;  // no device visible (sizing on a host without a GPU): GB300's count
+  }
+  return nsm;
+}
+
+int dense_supported_K(int K) {
+  if (K >= 1 && K <= 1024) return 1;
+  WideGeom g;
+  return wide_geometry(K, device_sm_count(), &g) ? 1 : 0;
+}
 
 // Streamed configurations (K > 256) read logA from a row-pair copy
 // Ap[i/2][c] = (A[i][c], A[i+1][c]), rows padded to the configuration's row
 // count and columns to cluster x 128, padding -inf.
 void dense_stream_geometry(int K, int* KPM, int* cols) {
   if (K <= 256) { *KPM = 0; *cols = 0; return; }
+  if (K > 1024) {
+    WideGeom g;
+    if (!wide_geometry(K, device_sm_count(), &g)) { *KPM = 0; *cols = 0; return; }
+    *KPM = g.KR;
+    *cols = g.NCB * 128;
+    return;
+  }
   if (K <= 512) { *KPM = 512; *cols = 512; return; }
   *KPM = 1024;
   *cols = 1024;
@@ -921,6 +941,7 @@ cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st
 
 // Rows padded to a multiple of 4 * NW for the chosen configuration.
 cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st) {
+  if (a.K > 1024) return launch_wide_forward(a, st);
   if (a.K <= 64) return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
   if (a.K <= 128) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
   if (a.K <= 256) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);

@@ -68,7 +68,21 @@ struct DenseArgs {
   const float2* Ap;           // streamed configurations: row-pair copy of logA
   int64_t ap_stride;          // float2 per row pair of Ap
   float* snap_scratch;        // streamed configurations: sub snapshots [clusters][S][rows]
+  // whole-GPU configuration (K > 1024): delta / MidState double buffers,
+  // sub snapshots by job parity (each [2][lanes][K]) and per-CTA step flags
+  float* wide_D;
+  uint16_t* wide_M;
+  float* wide_X;
+  uint32_t* wide_flags;
   WsHeader* hdr;
+};
+
+// Geometry of the whole-GPU engine for one K (fv_wide.cu); it advances
+// kWideLanes jobs in lockstep.
+constexpr int kWideLanes = 8;
+struct WideGeom {
+  int32_t CR, NCB, G, KR, RPC, RPW, RWR;  // cluster size, column blocks, CTAs, padded rows, rows per CTA / warp, resident rows per warp
+  size_t smem;                            // dynamic shared memory per CTA
 };
 
 // Beam search and FLASH-BS (fv_beam.cu).
@@ -125,6 +139,10 @@ struct ScoreArgs {
 };
 
 int dense_supported_K(int K);
+int device_sm_count();
+bool wide_geometry(int K, int nsm, WideGeom* g);
+size_t wide_scratch_bytes(int K, int nsm);
+cudaError_t launch_wide_forward(DenseArgs a, cudaStream_t st);
 void dense_stream_geometry(int K, int* KPM, int* cols);
 cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st);
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t st);
