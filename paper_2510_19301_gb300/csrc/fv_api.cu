@@ -499,7 +499,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
       }
       if (md.K > 1024) {
         // whole-GPU engine scratch: the same carving as wide_scratch_bytes
-        const size_t lanes_k = (size_t)kWideLanes * md.K;
+        const size_t lanes_k = (size_t)kWideLanes * wide_lane_stride(md.K);
         char* w = ws + L.wide;
         da.wide_D = reinterpret_cast<float*>(w);
         w += align_up(2 * sizeof(float) * lanes_k);

@@ -80,9 +80,12 @@ struct DenseArgs {
 // Geometry of the whole-GPU engine for one K (fv_wide.cu); it advances
 // kWideLanes jobs in lockstep.
 constexpr int kWideLanes = 8;
+// Elements per lane in the engine's global delta / MidState / snapshot rows.
+__host__ __device__ inline int wide_lane_stride(int K) { return (K + 31) / 32 * 32; }
 struct WideGeom {
   int32_t CR, NCB, G, KR, RPC, RPW, RWR;  // cluster size, column blocks, CTAs, padded rows, rows per CTA / warp, resident rows per warp
   size_t smem;                            // dynamic shared memory per CTA
+  float l2_keep;                          // fraction of streamed logA lines loaded with L2 evict_last priority
 };
 
 // Beam search and FLASH-BS (fv_beam.cu).

@@ -87,6 +87,33 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// L2 policy: a fraction of the lines gets evict_last priority, the rest
+// keep their normal priority (a streamed logA larger than L2 would otherwise
+// evict itself every step).
+__device__ __forceinline__ uint64_t l2_keep_policy(float frac) {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_unchanged.b64 %0, %1;" : "=l"(p) : "f"(frac));
+  return p;
+}
+__device__ __forceinline__ void cp_async16_keep(void* smem_dst, const void* gmem_src, uint64_t pol) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long ldg64_keep(const unsigned long long* p, uint64_t pol) {
+  unsigned long long v;
+  asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+// Bytes of logA the whole grid streams per step, and the share of them to
+// keep in L2 (about 48 MB of a 126 MB L2 is left to the rest of the step).
+float wide_l2_keep(const WideGeom& g) {
+  const double streamed = (double)g.G * kWNW * (g.RPW - g.RWR) * kWJ * sizeof(float);
+  if (streamed <= 0) return 1.f;
+  const double f = 48.0e6 / streamed;
+  return f >= 1.0 ? 1.f : (float)f;
+}
+
 __host__ __device__ inline int32_t wpe(int32_t T, int32_t P) {
   if (T <= 1) return 1;
   int32_t p = P < 2 ? 2 : P;
@@ -96,23 +123,63 @@ __host__ __device__ inline int32_t wdiv(int32_t k, int32_t T, int32_t Pe) {
   return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
 }
 
+template <int CR>
+__global__ void wide_fwd_kernel(DenseArgs a, WideGeom g);
+
+// Clusters of CR CTAs (one CTA per SM) that can be resident at once: a
+// cluster must fit inside one GPC, so this is below nsm / CR.  Queried once
+// per process; without a usable device the plain bound nsm / CR is used.
+static int max_wide_clusters(int CR, int nsm) {
+  static int cache[3] = {-1, -1, -1};
+  const int slot = CR == 2 ? 0 : (CR == 4 ? 1 : 2);
+  if (cache[slot] >= 0) return cache[slot];
+  int n = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CR;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CR * nsm);
+  cfg.blockDim = dim3(kWNW * 32);
+  cfg.dynamicSmemBytes = kWSmemMax;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaSuccess;
+  if (CR == 2) {
+    e = cudaFuncSetAttribute(wide_fwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemMax);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, wide_fwd_kernel<2>, &cfg);
+  } else if (CR == 4) {
+    e = cudaFuncSetAttribute(wide_fwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemMax);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, wide_fwd_kernel<4>, &cfg);
+  } else {
+    e = cudaFuncSetAttribute(wide_fwd_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemMax);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, wide_fwd_kernel<8>, &cfg);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    n = nsm / CR;
+  }
+  cache[slot] = n;
+  return n;
+}
+
 bool wide_geometry(int K, int nsm, WideGeom* g) {
   if (K <= 1024) return false;
   g->NCB = (K + kWJ - 1) / kWJ;
-  // clusters must fit inside GPCs: at most 16 of 8 CTAs or 32 of 4 CTAs
-  // are co-resident on a 152-SM part
-  if (g->NCB <= 16 && g->NCB * 8 <= nsm) g->CR = 8;
-  else if (g->NCB <= 32 && g->NCB * 4 <= nsm) g->CR = 4;
+  // the largest cluster size whose clusters can all be co-resident
+  if (g->NCB <= max_wide_clusters(8, nsm)) g->CR = 8;
+  else if (g->NCB <= max_wide_clusters(4, nsm)) g->CR = 4;
+  else if (g->NCB <= max_wide_clusters(2, nsm)) g->CR = 2;
   else return false;
   const int gran = g->CR * kWNW * kWCH;
   g->KR = (K + gran - 1) / gran * gran;
   g->RPC = g->KR / g->CR;
   g->RPW = g->RPC / kWNW;
   const size_t sD = sizeof(float) * (size_t)kWS * (g->RPC + g->RPC / 8);
-  const size_t sMid = sizeof(uint16_t) * (size_t)kWS * g->RPC;
   const size_t ring = sizeof(float2) * (size_t)kWNW * kWNST * 2 * kWJ;
   const size_t recv = 2 * sizeof(float) * 2 * (size_t)kWS * kWJ;
-  const size_t fixed = sD + sMid + ring + recv;
+  const size_t fixed = sD + ring + recv;
   if (fixed + 4096 > (size_t)kWSmemMax) return false;
   int rwr = (int)((kWSmemMax - fixed) / ((size_t)kWNW * kWJ * sizeof(float)));
   rwr &= ~3;
@@ -121,25 +188,34 @@ bool wide_geometry(int K, int nsm, WideGeom* g) {
   g->RWR = rwr;
   g->smem = fixed + sizeof(float) * (size_t)kWNW * rwr * kWJ;
   g->G = g->NCB * g->CR;
+  g->l2_keep = wide_l2_keep(*g);
   return true;
 }
 
 size_t wide_scratch_bytes(int K, int nsm) {
   // delta and MidState double buffers, sub snapshots (job parity), flags
-  return align_up(2 * sizeof(float) * (size_t)kWS * K) + align_up(2 * sizeof(uint16_t) * (size_t)kWS * K) +
-         align_up(2 * sizeof(float) * (size_t)kWS * K) + align_up(sizeof(uint32_t) * 8 * (size_t)(nsm + 1));
+  const size_t lk = (size_t)kWS * wide_lane_stride(K);
+  return align_up(2 * sizeof(float) * lk) + align_up(2 * sizeof(uint16_t) * lk) + align_up(2 * sizeof(float) * lk) +
+         align_up(sizeof(uint32_t) * 8 * (size_t)(nsm + 1));
 }
 
 template <int CR>
 __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom g) {
+  static_assert(CR == 2 || CR == 4 || CR == 8, "cluster sizes 2, 4, 8");
   constexpr int JO = kWJ / CR;  // targets owned per CTA
+  constexpr int OPW = (kWS * JO + kWNT - 1) / kWNT;  // owned outputs per thread
   extern __shared__ __align__(16) float smem[];
   __shared__ WLane lanes[kWS];
   __shared__ WDesc wdesc[kWS];
   __shared__ int s_njobs, s_abort_local;
   __shared__ uint32_t s_abort[2][CR];
 
-  if (a.hdr->status != 0) return;  // uniform: no CTA has started any wait
+  // the launch must have exactly the planned shape (every index below
+  // depends on it); gridDim and the cluster size are the same in every CTA
+  if (gridDim.x != (unsigned)g.G || cluster_nctarank() != (unsigned)CR) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(a.hdr, FV_EUNSUPPORTED, 0x57100000u);
+    return;
+  }
 
   const int K = a.K, RPC = g.RPC, RPW = g.RPW, RWR = g.RWR, RPCS = RPC + RPC / 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -148,11 +224,12 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
   const int j0 = cl * kWJ;
   const int row0 = (int)rank * RPC;
   const int kind = a.kind;
-  const int64_t SK = (int64_t)kWS * K;
+  const int KD = wide_lane_stride(K);  // lane stride of the global rows
+  const uint64_t pol = l2_keep_policy(g.l2_keep);
+  const int64_t SK = (int64_t)kWS * KD;
 
   float* sD = smem;                                                        // [S][RPCS] skewed rows
-  uint16_t* sMid = reinterpret_cast<uint16_t*>(sD + kWS * RPCS);           // [S][RPC]
-  float2* sRing = reinterpret_cast<float2*>(sMid + kWS * RPC);             // [NW][NST][2][J]
+  float2* sRing = reinterpret_cast<float2*>(sD + kWS * RPCS);              // [NW][NST][2][J]
   float* sRV = reinterpret_cast<float*>(sRing + kWNW * kWNST * 2 * kWJ);   // [2][CR][S][JO]
   uint32_t* sRI = reinterpret_cast<uint32_t*>(sRV + 2 * kWS * kWJ);        // [2][CR][S][JO]
   float2* sA = reinterpret_cast<float2*>(sRI + 2 * kWS * kWJ);             // [NW][RWR/2][J]
@@ -176,6 +253,16 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
   const int c_lo = row0 / kWJ, c_hi = rows_hi > row0 ? (rows_hi - 1) / kWJ : -1;
   const int nprod = c_hi >= c_lo ? (c_hi - c_lo + 1) * CR : 0;
   cluster_sync_all();
+  // an earlier kernel may have recorded an error: every CTA of the cluster
+  // takes the same decision (the OR of what each of them read)
+  if (tid < CR) dsmem_st_u32(dsmem_addr(&s_abort[1][rank], tid), a.hdr->status != 0 ? 1u : 0u);
+  cluster_sync_all();
+  {
+    uint32_t bad = 0;
+#pragma unroll
+    for (int rr = 0; rr < CR; ++rr) bad |= s_abort[1][rr];
+    if (bad) return;  // no peer touches this CTA's shared memory any more
+  }
 
   uint32_t tau = 0;
   for (;;) {
@@ -273,16 +360,21 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
     if (!__syncthreads_or(live)) break;
     const int any_term = __syncthreads_or(tid < kWS && lanes[tid].term);
 
-    // ---- owner-side prefetch of E_t (and the start terms of first steps)
-    const int os = tid / JO, ol = tid % JO, oj = j0 + (int)rank * JO + ol;
-    float ev = 0.f, pv = 0.f, av = 0.f;
-    if (tid < kWS * JO) {
-      const WDesc& d = wdesc[os];
-      if (d.mode && oj < K) {
-        ev = a.emit == FV_EMIT_DENSE ? __ldg(d.erow + oj) : __ldg(a.logB + (int64_t)oj * a.V + d.sym);
-        if (d.mode == 1) {
-          if (d.first) pv = __ldg(a.log_pi + oj);
-          else av = __ldg(a.logA + (int64_t)d.q_prev * K + oj);
+    // ---- owner-side prefetch of E_t (and the start terms of first steps);
+    // output o = tid + kWNT * u of this CTA is (lane o / JO, target o % JO)
+    float ev[OPW], pv[OPW], av[OPW];
+#pragma unroll
+    for (int u = 0; u < OPW; ++u) {
+      const int o = tid + kWNT * u, os = o / JO, oj = j0 + (int)rank * JO + o % JO;
+      ev[u] = pv[u] = av[u] = 0.f;
+      if (o < kWS * JO) {
+        const WDesc& d = wdesc[os];
+        if (d.mode && oj < K) {
+          ev[u] = a.emit == FV_EMIT_DENSE ? __ldg(d.erow + oj) : __ldg(a.logB + (int64_t)oj * a.V + d.sym);
+          if (d.mode == 1) {
+            if (d.first) pv[u] = __ldg(a.log_pi + oj);
+            else av[u] = __ldg(a.logA + (int64_t)d.q_prev * K + oj);
+          }
         }
       }
     }
@@ -318,7 +410,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
         const int s = warp;  // kWNW == kWS
         if (lanes[s].term) {
           const WJob& jb = lanes[s].old;
-          const float* dl = a.wide_D + cur * SK + (int64_t)s * K;
+          const float* dl = a.wide_D + cur * SK + (int64_t)s * KD;
           if (kind == kJobVanilla) {
             float bv = -CUDART_INF_F;
             int bi = 0x7fffffff;
@@ -337,31 +429,31 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
             }
           } else if (kind == kJobSub && lane == 0) {
             const int tmid = (jb.m + jb.n) / 2;
-            int q = a.wide_M[cur * SK + (int64_t)s * K + jb.q_n];
+            int q = a.wide_M[cur * SK + (int64_t)s * KD + jb.q_n];
             q = (unsigned)q < (unsigned)K ? q : 0;
             a.paths[jb.path_off + tmid] = q;
-            a.sval[jb.aux_off + tmid] = a.wide_X[(int64_t)jb.par * SK + (int64_t)s * K + q];
+            a.sval[jb.aux_off + tmid] = a.wide_X[(int64_t)jb.par * SK + (int64_t)s * KD + q];
           }
         }
       }
-      // ---- delta_{t-1} (and MidState_{t-1}) of this CTA's rows
+      // ---- delta_{t-1} of this CTA's rows, 16-byte asynchronous copies
+      // into the skewed layout (-inf beyond K)
       for (int s = 0; s < kWS; ++s) {
-        const WDesc& d = wdesc[s];
-        if (d.mode != 2) continue;
-        const float* src = a.wide_D + cur * SK + (int64_t)s * K;
+        if (wdesc[s].mode != 2) continue;
+        const float* src = a.wide_D + cur * SK + (int64_t)s * KD + row0;
         float* dst = sD + s * RPCS;
-        for (int x = tid; x < RPC; x += kWNT) {
-          const int i = row0 + x;
-          dst[x + ((x >> 5) << 2)] = i < K ? src[i] : -CUDART_INF_F;
-        }
-        if (d.f_mid == 2) {
-          const uint16_t* ms = a.wide_M + cur * SK + (int64_t)s * K;
-          for (int x = tid; x < RPC; x += kWNT) {
-            const int i = row0 + x;
-            sMid[s * RPC + x] = i < K ? ms[i] : (uint16_t)0;
+        for (int x4 = tid * 4; x4 < RPC; x4 += kWNT * 4) {
+          float* dp = dst + x4 + ((x4 >> 5) << 2);
+          if (row0 + x4 + 3 < K) {
+            cp_async16(dp, src + x4);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dp[u] = row0 + x4 + u < K ? src[x4 + u] : -CUDART_INF_F;
           }
         }
       }
+      cp_async_commit();
+      cp_async_wait<0>();
       __syncthreads();
 
       // ---- main loop: value-only tropical product over this warp's RPW
@@ -424,7 +516,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int qq = lane + 32 * u, pr = qq / (kWJ / 2), c2 = (qq % (kWJ / 2)) * 2;
-            cp_async16(dst + pr * kWJ + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
+            cp_async16_keep(dst + pr * kWJ + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2, pol);
           }
         };
 #pragma unroll
@@ -459,17 +551,16 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
       }
       __syncthreads();
 
-      // ---- merge over warps, exact re-scan of the winning chunk, send
-      // (value, row, ancestor) to the target's owner
+      // ---- merge over warps: per (lane, target) the maximum and the first
+      // chunk reaching it, sent to the target's owner
       {
         const int jj = tid % kWJ, s0 = tid / kWJ;
         const int orank = jj / JO, ojl = jj % JO;
-#pragma unroll 1
+#pragma unroll
         for (int s = s0; s < kWS; s += kWNT / kWJ) {
-          const WDesc& d = wdesc[s];
-          if (d.mode != 2) continue;
+          if (wdesc[s].mode != 2) continue;
           float bv = -CUDART_INF_F;
-          int wb = 0;
+          uint32_t wb = 0;
 #pragma unroll
           for (int w = 0; w < kWNW; ++w) {
             const float* pvw = reinterpret_cast<const float*>(sRing + w * kWNST * 2 * kWJ);
@@ -477,31 +568,13 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
             const float v = pvw[s * kWJ + jj];
             if (w == 0 || v > bv) { bv = v; wb = pcw[s * kWJ + jj]; }
           }
-          const int cb = wb * kWCH;  // first local row of the chunk
-          const float* dr = sD + s * RPCS + cb + ((cb >> 5) << 2);
-          const unsigned long long* ar =
-              reinterpret_cast<const unsigned long long*>(a.Ap + (int64_t)((row0 + cb) / 2) * a.ap_stride + j0 + jj);
-          unsigned long long avv[kWCH / 2];
-#pragma unroll
-          for (int k2 = 0; k2 < kWCH / 2; ++k2) avv[k2] = __ldg(ar + (int64_t)k2 * a.ap_stride);
-          int arg = cb;
-          float val = bv;
-#pragma unroll
-          for (int k2 = kWCH / 2 - 1; k2 >= 0; --k2) {
-            float c0, c1;
-            wfadd2(*reinterpret_cast<const unsigned long long*>(dr + 2 * k2), avv[k2], c0, c1);
-            if (c1 == bv) { arg = cb + 2 * k2 + 1; val = c1; }
-            if (c0 == bv) { arg = cb + 2 * k2; val = c0; }
-          }
-          const uint32_t m16 = d.f_mid == 2 ? (uint32_t)sMid[s * RPC + arg] : 0u;
-          const uint32_t im = (uint32_t)(row0 + arg) | (m16 << 16);
           const int off = ((cur * CR + (int)rank) * kWS + s) * JO + ojl;
           if (orank == (int)rank) {
-            sRV[off] = val;
-            sRI[off] = im;
+            sRV[off] = bv;
+            sRI[off] = wb;
           } else {
-            dsmem_st_f32(dsmem_addr(sRV + off, orank), val);
-            dsmem_st_u32(dsmem_addr(sRI + off, orank), im);
+            dsmem_st_f32(dsmem_addr(sRV + off, orank), bv);
+            dsmem_st_u32(dsmem_addr(sRI + off, orank), wb);
           }
         }
       }
@@ -516,41 +589,80 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
     if (abort_any) break;
 
     // ---- owners: lowest rank holding the maximum, + E_t, stores
-    if (tid < kWS * JO) {
-      const WDesc& d = wdesc[os];
-      if (d.mode && oj < K) {
-        float dval;
-        uint32_t mnew = 0;
-        if (d.mode == 1) {
-          if (d.first) dval = __fadd_rn(pv, ev);
-          else dval = a.complete ? __fadd_rn(av, ev) : __fadd_rn(__fadd_rn(d.s_prev, av), ev);
-        } else {
-          int base = (cur * CR * kWS + os) * JO + ol;
-          float bv = sRV[base];
-          uint32_t bi = sRI[base];
 #pragma unroll
-          for (int rr = 1; rr < CR; ++rr) {
-            const float v = sRV[base + rr * kWS * JO];
-            if (v > bv) { bv = v; bi = sRI[base + rr * kWS * JO]; }
-          }
-          const uint32_t ag = bi & 0xffffu;
-          dval = __fadd_rn(bv, ev);
-          if (kind == kJobVanilla) a.psi[d.psi_row + oj] = (uint16_t)ag;
-          if (d.f_mid) {
-            mnew = d.f_mid == 1 ? ag : (bi >> 16);
-            a.wide_M[nxt * SK + (int64_t)os * K + oj] = (uint16_t)mnew;
-          }
+    for (int u = 0; u < OPW; ++u) {
+      const int o = tid + kWNT * u, os = o / JO, ol = o % JO, oj = j0 + (int)rank * JO + ol;
+      if (o >= kWS * JO) continue;
+      const WDesc& d = wdesc[os];
+      if (!d.mode || oj >= K) continue;
+      float dval;
+      uint32_t mnew = 0;
+      if (d.mode == 1) {
+        if (d.first) dval = __fadd_rn(pv[u], ev[u]);
+        else dval = a.complete ? __fadd_rn(av[u], ev[u]) : __fadd_rn(__fadd_rn(d.s_prev, av[u]), ev[u]);
+      } else {
+        // the lowest rank holding the maximum, then its first chunk reaching
+        // it: re-scan those 32 rows (descending, so the last match is the
+        // lowest row); the kept value is the recomputed candidate
+        const int base = (cur * CR * kWS + os) * JO + ol;
+        float bv = sRV[base];
+        int rb = 0;
+#pragma unroll
+        for (int rr = 1; rr < CR; ++rr) {
+          const float v = sRV[base + rr * kWS * JO];
+          if (v > bv) { bv = v; rb = rr; }
         }
-        if (d.f_snap) {
-          if (kind == kJobRoot) {
-            a.snaps[d.snap_row + oj] = dval;
-            if (d.map_row >= 0) a.maps[d.map_row + oj] = (uint16_t)mnew;
-          } else {
-            a.wide_X[(int64_t)d.par * SK + (int64_t)os * K + oj] = dval;
-          }
+        const int rowc = rb * RPC + (int)sRI[base + rb * kWS * JO] * kWCH;
+        const float4* dsrc = reinterpret_cast<const float4*>(a.wide_D + cur * SK + (int64_t)os * KD + rowc);
+        const unsigned long long* asrc =
+            reinterpret_cast<const unsigned long long*>(a.Ap + (int64_t)(rowc / 2) * a.ap_stride + oj);
+        float4 dv[kWCH / 4];
+        unsigned long long avv[kWCH / 2];
+#pragma unroll
+        for (int k2 = 0; k2 < kWCH / 4; ++k2) dv[k2] = dsrc[k2];
+#pragma unroll
+        for (int k2 = 0; k2 < kWCH / 2; ++k2) avv[k2] = ldg64_keep(asrc + (int64_t)k2 * a.ap_stride, pol);
+        uint4 mv[kWCH / 8];
+#pragma unroll
+        for (int k2 = 0; k2 < kWCH / 8; ++k2) mv[k2] = make_uint4(0u, 0u, 0u, 0u);
+        if (d.f_mid == 2) {
+          const uint4* msrc = reinterpret_cast<const uint4*>(a.wide_M + cur * SK + (int64_t)os * KD + rowc);
+#pragma unroll
+          for (int k2 = 0; k2 < kWCH / 8; ++k2) mv[k2] = msrc[k2];
         }
-        a.wide_D[nxt * SK + (int64_t)os * K + oj] = dval;
+        int arg = 0;
+        uint32_t mold = 0;  // MidState_{t-1} of the winning row
+        float val = bv;
+#pragma unroll
+        for (int k2 = kWCH / 2 - 1; k2 >= 0; --k2) {
+          const float4 q4 = dv[k2 / 2];
+          const float dlo = (k2 & 1) ? q4.z : q4.x, dhi = (k2 & 1) ? q4.w : q4.y;
+          const unsigned long long dpair =
+              ((unsigned long long)__float_as_uint(dhi) << 32) | (unsigned long long)__float_as_uint(dlo);
+          const uint4 m4 = mv[k2 / 4];
+          const uint32_t mw = (k2 & 3) == 0 ? m4.x : ((k2 & 3) == 1 ? m4.y : ((k2 & 3) == 2 ? m4.z : m4.w));
+          float c0, c1;
+          wfadd2(dpair, avv[k2], c0, c1);
+          if (c1 == bv) { arg = 2 * k2 + 1; val = c1; mold = mw >> 16; }
+          if (c0 == bv) { arg = 2 * k2; val = c0; mold = mw & 0xffffu; }
+        }
+        const uint32_t ag = (uint32_t)(rowc + arg);
+        dval = __fadd_rn(val, ev[u]);
+        if (kind == kJobVanilla) a.psi[d.psi_row + oj] = (uint16_t)ag;
+        if (d.f_mid) {
+          mnew = d.f_mid == 1 ? ag : mold;
+          a.wide_M[nxt * SK + (int64_t)os * KD + oj] = (uint16_t)mnew;
+        }
       }
+      if (d.f_snap) {
+        if (kind == kJobRoot) {
+          a.snaps[d.snap_row + oj] = dval;
+          if (d.map_row >= 0) a.maps[d.map_row + oj] = (uint16_t)mnew;
+        } else {
+          a.wide_X[(int64_t)d.par * SK + (int64_t)os * KD + oj] = dval;
+        }
+      }
+      a.wide_D[nxt * SK + (int64_t)os * KD + oj] = dval;
     }
     __syncthreads();
     if (tid == 0) {
@@ -607,7 +719,8 @@ cudaError_t launch_wide_forward(DenseArgs a, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, kern, a, g);
   };
   if (g.CR == 8) return run(wide_fwd_kernel<8>);
-  return run(wide_fwd_kernel<4>);
+  if (g.CR == 4) return run(wide_fwd_kernel<4>);
+  return run(wide_fwd_kernel<2>);
 }
 
 }  // namespace fv
