@@ -72,6 +72,8 @@ def _load():
         i32 = ctypes.c_int32
         lib.orc_viterbi.argtypes = [P, i32, P, P, P]
         lib.orc_flash.argtypes = [P, i32, P, i32, i32, P, P, P, P]
+        lib.orc_flash_budget.argtypes = [P, i32, P, i32, i32, ctypes.c_int64, P, P, P, P, P]
+        lib.orc_flash_budget.restype = ctypes.c_int
         lib.orc_beam.argtypes = [P, i32, P, i32, P, P]
         lib.orc_flash_bs.argtypes = [P, i32, P, i32, i32, i32, P, P, P]
         lib.orc_path_score.argtypes = [P, i32, P, P]
@@ -154,6 +156,23 @@ def flash(hmm: HMM, E, P: int, complete: bool = False):
     if rc:
         raise RuntimeError(f"orc_flash failed: {rc}")
     return path, score[0], log[: 3 * n[0]].reshape(-1, 3)
+
+
+def flash_budget(hmm: HMM, E, P: int, budget_rows: int, complete: bool = False):
+    """FLASH Viterbi whose tasks with n - m <= budget_rows are solved as
+    leaves (segment backpointers + backtrack) -> (path, score, n_tasks,
+    n_leaves)."""
+    E = _E(E, hmm.K)
+    T = E.shape[0]
+    path = np.zeros(T, np.int32)
+    score = np.zeros(1, np.float32)
+    n = np.zeros(1, np.int32)
+    nl = np.zeros(1, np.int32)
+    rc = _load().orc_flash_budget(hmm.ref, T, _ptr(E), int(P), int(complete), ctypes.c_int64(int(budget_rows)),
+                                  _ptr(path), _ptr(score), None, _ptr(n), _ptr(nl))
+    if rc:
+        raise RuntimeError(f"orc_flash_budget failed: {rc}")
+    return path, score[0], int(n[0]), int(nl[0])
 
 
 def beam(hmm: HMM, E, B: int):

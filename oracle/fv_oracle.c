@@ -258,11 +258,50 @@ static int32_t split_points(int32_t T, int32_t P, int32_t* e) {
 
 int32_t orc_split_points(int32_t T, int32_t P, int32_t* e) { return split_points(T, P, e); }
 
-/* FLASH Viterbi.  task_log (optional, 3*T ints) receives (m, n, tmid) of    */
-/* every subtask in processing order; *n_tasks their count.                 */
-int orc_flash(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t complete,
-              int32_t* path, float* score, int32_t* task_log, int32_t* n_tasks) {
-  if (!m || T < 1 || m->K < 1 || P < 1) return ORC_EINVAL;
+/* Budget leaf (the memory-bounded end of Alg. 1's recursion): a segment  */
+/* (m, n) whose backpointer rows psi_{m+1..n} fit the budget is decoded    */
+/* directly -- the same pruned start as a subtask (R4), the recursion of   */
+/* Sec. III-A with psi kept for the segment, then the backtrack from the   */
+/* known q*_n writes q*_{n-1} .. q*_m.                                      */
+static int flash_leaf(const orc_model* m, const float* E, const orc_task* tk, int32_t q_n, int complete,
+                      int32_t* path) {
+  const int32_t K = m->K, rows = tk->n - tk->m;
+  float* d0 = malloc(sizeof(float) * K);
+  float* d1 = malloc(sizeof(float) * K);
+  float* best = malloc(sizeof(float) * K);
+  int32_t* psi = malloc(sizeof(int32_t) * (size_t)(rows > 0 ? rows : 1) * K);
+  if (!d0 || !d1 || !best || !psi) { free(d0); free(d1); free(best); free(psi); return ORC_ENOMEM; }
+  const float* Em = E + (int64_t)tk->m * K;
+  if (tk->m == 0) {
+    for (int32_t j = 0; j < K; ++j) d0[j] = m->log_pi[j] + Em[j];
+  } else {
+    for (int32_t j = 0; j < K; ++j) {
+      float a = trans(m, tk->q_prev, j);
+      d0[j] = complete ? (a + Em[j]) : ((tk->s_prev + a) + Em[j]);
+    }
+  }
+  for (int32_t t = tk->m + 1; t <= tk->n; ++t) {
+    exact_step(m, d0, E + (int64_t)t * K, best, d1, psi + (int64_t)(t - tk->m - 1) * K);
+    float* tmp = d0; d0 = d1; d1 = tmp;
+  }
+  int32_t q = q_n;
+  for (int32_t t = tk->n; t > tk->m; --t) {
+    q = psi[(int64_t)(t - tk->m - 1) * K + q];
+    path[t - 1] = q;
+  }
+  free(d0); free(d1); free(best); free(psi);
+  return ORC_OK;
+}
+
+/* FLASH Viterbi with a backpointer budget of budget_rows rows of K      */
+/* entries: a dequeued task with n - m <= budget_rows is a leaf (above);    */
+/* budget_rows = 0 is the pure divide-and-conquer of Alg. 1.  task_log     */
+/* (optional, 3*T ints) receives (m, n, tmid) of every subtask in           */
+/* processing order; *n_tasks their count, *n_leaves the leaves solved.     */
+int orc_flash_budget(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t complete,
+                     int64_t budget_rows, int32_t* path, float* score, int32_t* task_log, int32_t* n_tasks,
+                     int32_t* n_leaves) {
+  if (!m || T < 1 || m->K < 1 || P < 1 || budget_rows < 0) return ORC_EINVAL;
   int32_t* e = malloc(sizeof(int32_t) * T);
   float* sval = malloc(sizeof(float) * T);
   orc_task* queue = malloc(sizeof(orc_task) * (size_t)T);
@@ -282,8 +321,14 @@ int orc_flash(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t 
     }
   }
   /* Task loop of Alg. 1 (serial FIFO order).                               */
+  int32_t leaves = 0;
   while (rc == ORC_OK && head < tail) {
     orc_task tk = queue[head++];
+    if ((int64_t)(tk.n - tk.m) <= budget_rows) {
+      rc = flash_leaf(m, E, &tk, path[tk.n], complete, path);
+      ++leaves;
+      continue;
+    }
     int32_t tmid = (tk.m + tk.n) / 2;
     int32_t qm; float sm;
     rc = flash_subtask(m, E, &tk, path[tk.n], complete, &qm, &sm);
@@ -299,8 +344,15 @@ int orc_flash(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t 
     }
   }
   if (n_tasks) *n_tasks = count;
+  if (n_leaves) *n_leaves = leaves;
   free(e); free(sval); free(queue);
   return rc;
+}
+
+/* FLASH Viterbi without a budget (Alg. 1 + Alg. 2 throughout).            */
+int orc_flash(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t complete,
+              int32_t* path, float* score, int32_t* task_log, int32_t* n_tasks) {
+  return orc_flash_budget(m, T, E, P, complete, 0, path, score, task_log, n_tasks, NULL);
 }
 
 /* ======================================================================== */

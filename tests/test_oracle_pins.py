@@ -295,6 +295,64 @@ def test_flash_complete_pruning_theorem3(oracle):
         assert abs(f64(pc) - f64(pv)) <= 1e-3
 
 
+@pytest.mark.parametrize("K,T", [(2, 8), (3, 6), (4, 5), (4, 8)])
+@pytest.mark.parametrize("budget", [1, 2, 3, 100])
+def test_flash_budget_leaves_match_brute_force(oracle, K, T, budget):
+    """Leaves (segment backpointers + backtrack from the known q_n) keep
+    the exact optimum: the path's score is the brute-force maximum and the
+    path is the vanilla one (lowest-index rule)."""
+    for seed in range(4):
+        log_pi, logA, E = W.random_small(K, T, seed=seed + 31 * K + T)
+        hmm = oracle.HMM(log_pi, logA)
+        pv, sv = oracle.viterbi(hmm, E)
+        _, scores = brute_scores(log_pi, logA, E)
+        for P in (1, 2, 3):
+            pb, sb, _, _ = oracle.flash_budget(hmm, E, P, budget)
+            idx = int(np.ravel_multi_index(tuple(int(q) for q in pb), (K,) * T))
+            assert scores[idx] == scores.max()
+            assert np.array_equal(pb, pv) and bits(sb) == bits(sv)
+
+
+@pytest.mark.parametrize("T,P", [(16, 4), (31, 3), (97, 7), (200, 16)])
+def test_flash_budget_task_accounting(oracle, T, P):
+    """Budget 0 is the pure divide-and-conquer (T - P' subtasks, no leaf).
+    A budget as large as any segment turns every first-level segment of
+    length >= 2 into a leaf and leaves no subtask.  In between, every
+    revealed state is still revealed exactly once (subtasks reveal one
+    midpoint each, a leaf of n - m rows reveals n - m states)."""
+    K = 4
+    log_pi, logA, E = W.random_small(K, T, seed=T + P)
+    hmm = oracle.HMM(log_pi, logA)
+    root = oracle.split_points(T, P)
+    Pe = len(root)
+    segs = [(0 if k == 0 else root[k - 1] + 1, root[k]) for k in range(Pe)]
+    segs = [(m, n) for m, n in segs if n - m >= 1]
+    _, _, n0, l0 = oracle.flash_budget(hmm, E, P, 0)
+    assert (n0, l0) == (T - Pe, 0)
+    _, _, n1, l1 = oracle.flash_budget(hmm, E, P, T)
+    assert (n1, l1) == (0, len(segs))
+    pv, sv = oracle.viterbi(hmm, E)
+    for budget in (1, 2, 3, 5, 9):
+        pb, sb, nt, nl = oracle.flash_budget(hmm, E, P, budget)
+        assert np.array_equal(pb, pv) and bits(sb) == bits(sv)
+        assert nt + nl >= len(segs) and nt <= T - Pe
+
+
+def test_flash_budget_integer_ties_neg_inf_and_complete(oracle):
+    for seed in range(30):
+        log_pi, logA, E = W.random_small(4, 29, seed=seed + 500, integer=True, lo=-1, hi=1,
+                                         neg_inf_frac=0.3 if seed % 2 else 0.0)
+        hmm = oracle.HMM(log_pi, logA)
+        pv, sv = oracle.viterbi(hmm, E)
+        for P, budget in ((1, 1), (3, 2), (4, 4), (8, 40)):
+            pb, sb, _, _ = oracle.flash_budget(hmm, E, P, budget)
+            assert np.array_equal(pv, pb) and bits(sv) == bits(sb)
+        # complete pruning with integer data: exact arithmetic, same path
+        pc, _, _, _ = oracle.flash_budget(hmm, E, 3, 2, complete=True)
+        if not np.isinf(sv):
+            assert np.array_equal(pv, pc)
+
+
 # --------------------------------------------------------------------------
 # Beam and FLASH-BS (Sec. V-C).
 
