@@ -61,19 +61,123 @@ const std::vector<int64_t>& level_counts(int64_t L, std::unordered_map<int64_t, 
   return memo.emplace(L, std::move(r)).first->second;
 }
 
+// Largest task length and total backpointer rows (n - m) per level below a
+// segment of length L: a task of length L has children of lengths
+// floor((L-1)/2)+1 and L - that (only the first when L == 3).
+struct LevelRows {
+  std::vector<int64_t> max_len, rows;
+};
+const LevelRows& level_rows(int64_t L, std::unordered_map<int64_t, LevelRows>& memo) {
+  auto it = memo.find(L);
+  if (it != memo.end()) return it->second;
+  LevelRows r;
+  if (L >= 2) {
+    r.max_len.push_back(L);
+    r.rows.push_back(L - 1);
+    const int64_t d = L - 1, left = d / 2 + 1, right = L - left;
+    auto add = [&](int64_t len) {
+      const LevelRows& c = level_rows(len, memo);
+      if (r.rows.size() < c.rows.size() + 1) {
+        r.rows.resize(c.rows.size() + 1, 0);
+        r.max_len.resize(c.rows.size() + 1, 0);
+      }
+      for (size_t k = 0; k < c.rows.size(); ++k) {
+        r.rows[k + 1] += c.rows[k];
+        r.max_len[k + 1] = std::max(r.max_len[k + 1], c.max_len[k]);
+      }
+    };
+    if (d > 2) { add(left); add(right); }
+    else if (d == 2) add(left);
+  }
+  return memo.emplace(L, std::move(r)).first->second;
+}
+
 struct FlashPlan {
   std::vector<int32_t> levels;      // per model: number of subtask levels
   std::vector<int64_t> max_tasks;   // per model: largest level
   int64_t list_cap = 0;             // entries per task list (max over models, >= level-1 lists)
   int32_t pe_max = 1, k_max = 1;
+  // budget leaves (exact FLASH with a backpointer budget): per model the
+  // first level whose every task's rows fit the budget (-1: none), the
+  // budget in rows, and an upper bound on the waves of that level
+  std::vector<int32_t> leaf_level, leaf_waves;
+  std::vector<int64_t> leaf_rows, leaf_tasks;
+  int32_t waves_max = 0;
+  size_t leaf_bytes = 0;
 };
 
-FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b, int32_t P) {
+// The sequence order of the device's order kernel (model asc, then T desc
+// unless nosort, then index asc), replayed from the host lengths.
+std::vector<int32_t> host_order(const fv_batch* b, bool nosort) {
+  std::vector<int32_t> o(b->n_seq);
+  for (int i = 0; i < b->n_seq; ++i) o[i] = i;
+  auto model = [&](int i) { return b->model_host ? b->model_host[i] : 0; };
+  std::sort(o.begin(), o.end(), [&](int x, int y) {
+    if (model(x) != model(y)) return model(x) < model(y);
+    if (!nosort && b->T_host[x] != b->T_host[y]) return b->T_host[x] > b->T_host[y];
+    return x < y;
+  });
+  return o;
+}
+
+// Waves of the budget-leaf level exactly as the device plans them: the
+// level's task list in device order (segments of each sequence in `order`,
+// then children in parent order), packed greedily into waves of at most R
+// backpointer rows.  Returns the wave count; *max_wave = the largest wave.
+int32_t host_leaf_waves(const fv_batch* b, const std::vector<int32_t>& order, int32_t model, int32_t P,
+                        int32_t level, int64_t R, int64_t* max_wave) {
+  std::vector<int32_t> cur, nxt;
+  for (int32_t i : order) {
+    if ((b->model_host ? b->model_host[i] : 0) != model) continue;
+    const int32_t T = b->T_host[i], Pe = pe_host(T, P);
+    int32_t prev = -1;
+    for (int k = 0; k < Pe; ++k) {
+      const int32_t e = (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
+      if (e - prev >= 2) cur.push_back(e - prev);
+      prev = e;
+    }
+  }
+  for (int l = 0; l < level; ++l) {
+    nxt.clear();
+    for (int32_t L : cur) {
+      const int32_t d = L - 1, left = d / 2 + 1;
+      if (d > 2) { nxt.push_back(left); nxt.push_back(L - left); }
+      else if (d == 2) nxt.push_back(left);
+    }
+    cur.swap(nxt);
+  }
+  int32_t waves = 0;
+  int64_t used = 0, first = 0;
+  *max_wave = 0;
+  for (size_t i = 0; i < cur.size(); ++i) {
+    const int64_t r = cur[i] - 1;
+    if (used + r > R && (int64_t)i > first) {
+      *max_wave = std::max<int64_t>(*max_wave, (int64_t)i - first);
+      ++waves;
+      first = (int64_t)i;
+      used = 0;
+    }
+    used += r;
+  }
+  if ((int64_t)cur.size() > first) {
+    *max_wave = std::max<int64_t>(*max_wave, (int64_t)cur.size() - first);
+    ++waves;
+  }
+  return waves;
+}
+
+FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b, int32_t P,
+                     uint64_t budget_bytes = 0, bool nosort = false) {
   FlashPlan fp;
   fp.levels.assign(n_models, 0);
   fp.max_tasks.assign(n_models, 0);
-  std::vector<std::vector<int64_t>> per(n_models);
+  fp.leaf_level.assign(n_models, -1);
+  fp.leaf_waves.assign(n_models, 0);
+  fp.leaf_rows.assign(n_models, 0);
+  fp.leaf_tasks.assign(n_models, 0);
+  std::vector<std::vector<int64_t>> per(n_models), maxlen(n_models), rows(n_models);
   std::unordered_map<int64_t, std::vector<int64_t>> memo;
+  std::unordered_map<int64_t, LevelRows> memo_rows;
   for (int i = 0; i < b->n_seq; ++i) {
     const int m = b->model_host ? b->model_host[i] : 0;
     const int32_t T = b->T_host[i], Pe = pe_host(T, P);
@@ -84,14 +188,41 @@ FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b
       const std::vector<int64_t>& c = level_counts(e - prev, memo);
       if (per[m].size() < c.size()) per[m].resize(c.size(), 0);
       for (size_t l = 0; l < c.size(); ++l) per[m][l] += c[l];
+      if (budget_bytes) {
+        const LevelRows& lr = level_rows(e - prev, memo_rows);
+        if (rows[m].size() < lr.rows.size()) {
+          rows[m].resize(lr.rows.size(), 0);
+          maxlen[m].resize(lr.rows.size(), 0);
+        }
+        for (size_t l = 0; l < lr.rows.size(); ++l) {
+          rows[m][l] += lr.rows[l];
+          maxlen[m][l] = std::max(maxlen[m][l], lr.max_len[l]);
+        }
+      }
       prev = e;
     }
   }
+  std::vector<int32_t> order;
   for (int m = 0; m < n_models; ++m) {
     if (models[m].K > fp.k_max) fp.k_max = models[m].K;
     fp.levels[m] = (int32_t)per[m].size();
     for (int64_t c : per[m]) fp.max_tasks[m] = std::max(fp.max_tasks[m], c);
     fp.list_cap = std::max(fp.list_cap, fp.max_tasks[m]);
+    if (!budget_bytes) continue;
+    const int64_t R = (int64_t)(budget_bytes / (2ull * (uint64_t)models[m].K));
+    for (size_t l = 0; l < rows[m].size() && R >= 1; ++l) {
+      const int64_t mr = maxlen[m][l] - 1;  // rows of the level's largest task
+      if (mr > R) continue;
+      fp.leaf_level[m] = (int32_t)l;
+      fp.leaf_rows[m] = R;
+      if (order.empty()) order = host_order(b, nosort);
+      int64_t mw = 0;
+      fp.leaf_waves[m] = host_leaf_waves(b, order, m, P, (int32_t)l, R, &mw);
+      fp.leaf_tasks[m] = mw;
+      fp.waves_max = std::max(fp.waves_max, fp.leaf_waves[m]);
+      fp.leaf_bytes = std::max(fp.leaf_bytes, (size_t)R * (size_t)models[m].K * sizeof(uint16_t));
+      break;
+    }
   }
   fp.list_cap = std::max<int64_t>(fp.list_cap, b->n_seq);
   return fp;
@@ -99,6 +230,7 @@ FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b
 
 struct Layout {
   size_t hdr, jobs, order, qlast, aux, aux2, maps, snaps, listA, listB, pos, bsum, counts, total;
+  size_t leaf, waves;  // budget leaves: backpointer area, wave [first | count] arrays
   size_t bscratch, div_id, div_val, div_mid, div_n;
   size_t ap, snapx;  // streamed exact configurations (K > 256)
   size_t wide;       // whole-GPU configuration scratch (K > 1024)
@@ -162,6 +294,11 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
     L.maps = end;
     L.snaps = align_up(L.maps + sizeof(uint16_t) * (size_t)L.map_stride * n);
     end = align_up(L.snaps + sizeof(float) * (size_t)L.snap_stride * n);
+    if (fp->leaf_bytes) {
+      L.leaf = end;
+      L.waves = align_up(L.leaf + fp->leaf_bytes);
+      end = align_up(L.waves + 2 * sizeof(int32_t) * (size_t)fp->waves_max);
+    }
   }
   if (mode != FV_BEAM) {
     // row-pair copy of the largest streamed model's logA, reused per model,
@@ -403,7 +540,8 @@ size_t fv_workspace_size(const fv_model* models, int32_t n_models, const fv_batc
   if (check_common(models, n_models, batch) != FV_OK) return 0;
   if (p->mode == FV_FLASH || (p->mode == FV_BEAM && p->P >= 1)) {
     if (p->P < 1 || (p->mode == FV_BEAM && p->B < 1)) return 0;
-    const FlashPlan fp = plan_flash(models, n_models, batch, p->P);
+    const FlashPlan fp = plan_flash(models, n_models, batch, p->P, p->mode == FV_FLASH ? p->mem_budget_bytes : 0,
+                                    (p->flags & FV_NO_SORT) != 0);
     return layout_for(models, n_models, batch, p->mode, &fp, p->B).total;
   }
   if (p->mode == FV_BEAM && p->B < 1) return 0;
@@ -430,7 +568,9 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   const int32_t n = batch->n_seq;
   const bool tasks = p->mode == FV_FLASH || (p->mode == FV_BEAM && p->P >= 1);
   FlashPlan fp;
-  if (tasks) fp = plan_flash(models, n_models, batch, p->P);
+  if (tasks)
+    fp = plan_flash(models, n_models, batch, p->P, p->mode == FV_FLASH ? p->mem_budget_bytes : 0,
+                    (p->flags & FV_NO_SORT) != 0);
   const Layout L = layout_for(models, n_models, batch, p->mode, tasks ? &fp : nullptr, p->B);
   if (batch->T_host && ws_bytes < L.total) return FV_ENOMEM;
   if (ws_bytes < L.aux) return FV_ENOMEM;
@@ -547,6 +687,31 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
       return FV_ECUDA;
     int c = 0;
     for (int lvl = 0; lvl < fp.levels[m]; ++lvl) {
+      if (lvl == fp.leaf_level[m]) {
+        // budget leaves: every task of this level keeps its own
+        // backpointer rows; waves of tasks whose rows fit the budget
+        int32_t* wave_first = reinterpret_cast<int32_t*>(ws + L.waves);
+        int32_t* wave_count = wave_first + fp.waves_max;
+        uint16_t* leaf = reinterpret_cast<uint16_t*>(ws + L.leaf);
+        if (launch_leaf_plan(lists[c], &counts[c], fp.leaf_rows[m], wave_first, wave_count, fp.leaf_waves[m], hdr,
+                             st) != cudaSuccess)
+          return FV_ECUDA;
+        for (int w = 0; w < fp.leaf_waves[m]; ++w) {
+          if (launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
+          da.kind = kJobLeaf;
+          da.tasks = lists[c];
+          da.task_first = &wave_first[w];
+          da.task_count = &wave_count[w];
+          da.psi = leaf;
+          da.max_jobs = (int32_t)fp.leaf_tasks[m];
+          if (launch_dense_forward(da, 0, st) != cudaSuccess) return FV_ECUDA;
+          if (launch_leaf_backtrack(lists[c], &wave_first[w], &wave_count[w], (int32_t)fp.leaf_tasks[m], jobs, md.K,
+                                    leaf, paths_out, hdr, st) != cudaSuccess)
+            return FV_ECUDA;
+        }
+        da.task_first = nullptr;
+        break;
+      }
       if (launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
       da.kind = kJobSub;
       da.tasks = lists[c];

@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           pj.b = pj.m = pj.n = pj.T = pj.Pe = pj.q_prev = pj.q_n = pj.pad = 0;
           pj.s_prev = 0.f;
           pj.e_off = pj.path_off = pj.aux_off = 0;
-          if (kind != kJobSub) {
+          const bool from_tasks = kind == kJobSub || kind == kJobLeaf;
+          if (!from_tasks) {
             if (k < (unsigned long long)a.order_count) {
               const int b = a.order[a.order_begin + (int)k];
               const Job jb = a.jobs[b];
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
               pj.aux_off = jb.aux_off;
             }
           } else if (k < (unsigned long long)*a.task_count) {
-            const Task tk = a.tasks[k];
+            const Task tk = a.tasks[(a.task_first ? *a.task_first : 0) + (int64_t)k];
             const Job jb = a.jobs[tk.b];
             pj.valid = 1;
             pj.b = tk.b;
@@ -340,6 +341,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
             pj.e_off = jb.e_off;
             pj.path_off = jb.path_off;
             pj.aux_off = jb.aux_off;
+            pj.pad = tk.pad;
             // states revealed by earlier levels; clamped so that no value can
             // index shared memory outside the slab
             const int qn = a.paths[jb.path_off + tk.n];
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         td.first = (t == 0);
         td.q_prev = jb.q_prev;
         td.s_prev = jb.s_prev;
-        td.psi_row = jb.aux_off + (int64_t)t * K;
+        td.psi_row = kind == kJobLeaf ? (int64_t)(jb.pad + t - jb.m - 1) * K : jb.aux_off + (int64_t)t * K;
         if (a.emit == FV_EMIT_DENSE) td.erow = a.E + jb.e_off + (int64_t)t * K;
         else td.sym = __ldg(a.obs + jb.e_off + t);
         if (kind == kJobRoot) {
@@ -676,7 +678,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         }
       } else {
         ag = arg[r] < K ? arg[r] : 0;  // only NaN inputs (unsupported) could leave it on a padded row
-        if (kind == kJobVanilla) {
+        if (kind == kJobVanilla || kind == kJobLeaf) {
           st_mask |= 1u << (2 * r);
           st_arg[r] = ag;
           st_off[r] = td.psi_row + jcol;

@@ -222,6 +222,109 @@ __global__ void __launch_bounds__(kScanBlock) child_pass3(const Task* in, const 
   }
 }
 
+// ---------------------------------------------------------- budget leaves
+// Greedy packing in list order: a task joins the current wave while the
+// wave's backpointer rows stay within budget_rows, else it opens the next
+// wave.  One block: the task rows of a chunk are staged in shared memory
+// and thread 0 walks them.
+constexpr int kLeafChunk = 4096;
+
+__global__ void __launch_bounds__(1024) leaf_plan_kernel(Task* tasks, const int32_t* count, int64_t budget_rows,
+                                                         int32_t* wave_first, int32_t* wave_count,
+                                                         int32_t max_waves, WsHeader* hdr) {
+  __shared__ int32_t rows[kLeafChunk];
+  __shared__ int32_t w_s, first_s;
+  __shared__ long long used_s;
+  const int n = *count;
+  if (threadIdx.x == 0) {
+    w_s = 0;
+    first_s = 0;
+    used_s = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base < n; base += kLeafChunk) {
+    const int cn = n - base < kLeafChunk ? n - base : kLeafChunk;
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) rows[i] = tasks[base + i].n - tasks[base + i].m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int w = w_s, first = first_s;
+      long long used = used_s;
+      for (int i = 0; i < cn; ++i) {
+        const int gi = base + i, r = rows[i];
+        if (used + r > budget_rows && gi > first) {
+          if (w < max_waves) {
+            wave_first[w] = first;
+            wave_count[w] = gi - first;
+          }
+          ++w;
+          first = gi;
+          used = 0;
+        }
+        rows[i] = (int32_t)used;  // the task's row offset in its wave
+        used += r;
+      }
+      w_s = w;
+      first_s = first;
+      used_s = used;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) tasks[base + i].pad = rows[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int w = w_s;
+    if (n > first_s) {
+      if (w < max_waves) {
+        wave_first[w] = first_s;
+        wave_count[w] = n - first_s;
+      }
+      ++w;
+    }
+    if (w > max_waves) set_status(hdr, FV_EUNSUPPORTED, 0x1eaf0000u | (uint32_t)w);
+    for (int k = w; k < max_waves; ++k) {
+      wave_first[k] = n;
+      wave_count[k] = 0;
+    }
+  }
+}
+
+// One warp per task; lane 0 follows the chain (each step is one dependent
+// 2-byte load, so the rows are not staged).
+__global__ void __launch_bounds__(128) leaf_backtrack_kernel(const Task* tasks, const int32_t* wave_first,
+                                                              const int32_t* wave_count, const Job* jobs,
+                                                              int32_t K, const uint16_t* leaf_psi, int32_t* paths,
+                                                              const WsHeader* hdr) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (hdr->status != 0 || idx >= *wave_count || lane != 0) return;
+  const Task tk = tasks[*wave_first + idx];
+  const Job jb = jobs[tk.b];
+  int32_t* path = paths + jb.path_off;
+  int q = path[tk.n];
+  q = (unsigned)q < (unsigned)K ? q : 0;
+  const uint16_t* base = leaf_psi + (int64_t)tk.pad * K;
+  for (int t = tk.n; t > tk.m; --t) {
+    q = base[(int64_t)(t - tk.m - 1) * K + q];
+    q = q < K ? q : 0;
+    path[t - 1] = q;
+  }
+}
+
+cudaError_t launch_leaf_plan(Task* tasks, const int32_t* count, int64_t budget_rows, int32_t* wave_first,
+                             int32_t* wave_count, int32_t max_waves, WsHeader* hdr, cudaStream_t st) {
+  leaf_plan_kernel<<<1, 1024, 0, st>>>(tasks, count, budget_rows, wave_first, wave_count, max_waves, hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_backtrack(const Task* tasks, const int32_t* wave_first, const int32_t* wave_count,
+                                  int32_t max_count, const Job* jobs, int32_t K, const uint16_t* leaf_psi,
+                                  int32_t* paths, const WsHeader* hdr, cudaStream_t st) {
+  if (max_count <= 0) return cudaSuccess;
+  leaf_backtrack_kernel<<<(max_count + 3) / 4, 128, 0, st>>>(tasks, wave_first, wave_count, jobs, K, leaf_psi, paths,
+                                                             hdr);
+  return cudaGetLastError();
+}
+
 __global__ void reset_counter(unsigned long long* pop) { *pop = 0ull; }
 
 cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st) {

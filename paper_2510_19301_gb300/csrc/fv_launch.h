@@ -27,7 +27,9 @@ enum JobKind : int32_t {
   kJobVanilla = 0,  // whole sequence, psi table (Sec. III-A)
   kJobRoot = 1,     // whole sequence, P' division points (Sec. V-A.3, Alg. 2 MidState)
   kJobSub = 2,      // segment task (m, n) of Alg. 1 with the pruned start of Sec. V-B.2
-  kJobBeam = 3      // whole sequence, beam with per-step backpointers (Sec. V-C, P = 0)
+  kJobBeam = 3,     // whole sequence, beam with per-step backpointers (Sec. V-C, P = 0)
+  kJobLeaf = 4      // segment task (m, n) solved with its own backpointer rows psi_{m+1..n}
+                    // (budget leaf); rows start at element task.pad * K of the leaf area
 };
 
 // One divide-and-conquer task (Alg. 1 tuple) of sequence b.
@@ -50,11 +52,12 @@ struct DenseArgs {
   const int32_t* order;       // vanilla/root: sequences in order[order_begin ..]
   int32_t order_begin;
   int32_t order_count;
-  const Task* tasks;          // sub: task list and its device-side count
+  const Task* tasks;          // sub / leaf: task list and its device-side count
   const int32_t* task_count;
+  const int32_t* task_first;  // sub / leaf: device-side index of the first task (null: 0)
   int32_t max_jobs;           // host upper bound of jobs (grid sizing)
   unsigned long long* pop;
-  uint16_t* psi;              // vanilla: backpointer rows at job.aux_off
+  uint16_t* psi;              // vanilla: backpointer rows at job.aux_off; leaf: the leaf area
   int32_t* qlast;             // vanilla: final states
   float* scores;              // vanilla: scores
   int32_t* paths;             // flash: revealed states (paths_out)
@@ -169,6 +172,17 @@ cudaError_t launch_level1_tasks(const Job* jobs, const int32_t* order, int32_t b
 cudaError_t launch_child_tasks(const Task* in, const int32_t* in_count, int32_t max_in, Task* out,
                                int32_t* out_count, ScanTmp tmp, unsigned long long* pop_reset, cudaStream_t st);
 cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st);
+// Budget leaves: greedy packing of a task list into waves whose backpointer
+// rows (n - m per task) fit budget_rows; writes each task's row offset into
+// Task::pad and the waves' [first, count) into wave_first / wave_count
+// (max_waves entries, unused ones empty).
+cudaError_t launch_leaf_plan(Task* tasks, const int32_t* count, int64_t budget_rows, int32_t* wave_first,
+                             int32_t* wave_count, int32_t max_waves, WsHeader* hdr, cudaStream_t st);
+// q_{t-1} = psi_t[q_t] from the known q_n down to t = m + 1 for every task of
+// one wave (max_count bounds the wave's size).
+cudaError_t launch_leaf_backtrack(const Task* tasks, const int32_t* wave_first, const int32_t* wave_count,
+                                  int32_t max_count, const Job* jobs, int32_t K, const uint16_t* leaf_psi,
+                                  int32_t* paths, const WsHeader* hdr, cudaStream_t st);
 size_t beam_scratch_stride(int K, int Bcap);
 int beam_max_ctas();
 cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st);

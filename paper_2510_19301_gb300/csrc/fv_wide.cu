@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
     lanes[tid].state = 0;
     lanes[tid].term = 0;
   }
-  if (tid == 0) s_njobs = kind == kJobSub ? *a.task_count : a.order_count;
+  const bool from_tasks = kind == kJobSub || kind == kJobLeaf;
+  const int task0 = from_tasks && a.task_first ? *a.task_first : 0;
+  if (tid == 0) s_njobs = from_tasks ? *a.task_count : a.order_count;
   if (tid < 2 * CR) s_abort[tid / CR][tid % CR] = 0;
   // producers of this CTA's rows: every CTA of the clusters covering them
   const int rows_hi = row0 + RPC < K ? row0 + RPC : K;
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
           j.q_prev = j.q_n = 0;
           j.s_prev = 0.f;
           j.par = L.k & 1;
-          if (kind != kJobSub) {
+          if (!from_tasks) {
             const int b = a.order[a.order_begin + gi];
             const Job jb = a.jobs[b];
             j.b = b;
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
             j.path_off = jb.path_off;
             j.aux_off = jb.aux_off;
           } else {
-            const Task tk = a.tasks[gi];
+            const Task tk = a.tasks[task0 + gi];
             const Job jb = a.jobs[tk.b];
             j.b = tk.b;
             j.m = tk.m;
@@ -306,6 +308,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
             j.e_off = jb.e_off;
             j.path_off = jb.path_off;
             j.aux_off = jb.aux_off;
+            j.pad = tk.pad;
             const int qn = a.paths[jb.path_off + tk.n];
             j.q_n = (unsigned)qn < (unsigned)K ? qn : 0;
             if (tk.m > 0) {
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
         d.q_prev = jb.q_prev;
         d.s_prev = jb.s_prev;
         d.par = jb.par;
-        d.psi_row = jb.aux_off + (int64_t)t * K;
+        d.psi_row = kind == kJobLeaf ? (int64_t)(jb.pad + t - jb.m - 1) * K : jb.aux_off + (int64_t)t * K;
         if (a.emit == FV_EMIT_DENSE) d.erow = a.E + jb.e_off + (int64_t)t * K;
         else d.sym = __ldg(a.obs + jb.e_off + t);
         if (kind == kJobRoot) {
@@ -648,7 +651,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
         }
         const uint32_t ag = (uint32_t)(rowc + arg);
         dval = __fadd_rn(val, ev[u]);
-        if (kind == kJobVanilla) a.psi[d.psi_row + oj] = (uint16_t)ag;
+        if (kind == kJobVanilla || kind == kJobLeaf) a.psi[d.psi_row + oj] = (uint16_t)ag;
         if (d.f_mid) {
           mnew = d.f_mid == 1 ? ag : mold;
           a.wide_M[nxt * SK + (int64_t)os * KD + oj] = (uint16_t)mnew;

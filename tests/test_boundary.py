@@ -111,3 +111,39 @@ def test_empty_batch_is_ok_without_device_work(lib):
     p = _params()
     assert lib.fv_decode(m, 1, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(0x100000), 1 << 20,
                          None, None, None) == L.FV_OK
+
+
+def test_flash_budget_workspace_accounting():
+    """The budget adds at most the budget itself (plus the wave table) to the
+    FLASH workspace, and none at all when it is below one backpointer row."""
+    import ctypes
+    from paper_2510_19301_gb300 import _lib as L
+    lib = L.load()
+    K = 256
+    lengths = np.array([1000, 2000, 3000, 500], np.int32)
+    m = L.fv_model()
+    m.K = K
+    m.trans = L.FV_TRANS_DENSE
+    m.emit = L.FV_EMIT_DENSE
+    m.log_pi = ctypes.c_void_p(256)
+    m.logA = ctypes.c_void_p(256)
+    b = L.fv_batch()
+    b.n_seq = len(lengths)
+    b.T_host = lengths.ctypes.data_as(ctypes.c_void_p)
+    for f in ("T", "e_off", "E", "path_off"):
+        setattr(b, f, ctypes.c_void_p(256))
+
+    def ws(budget):
+        p = L.fv_params()
+        p.mode = L.FV_FLASH
+        p.P = 16
+        p.mem_budget_bytes = budget
+        return lib.fv_workspace_size(ctypes.byref(m), 1, ctypes.byref(b), ctypes.byref(p))
+
+    base = ws(0)
+    assert base > 0
+    assert ws(2 * K - 1) == base
+    table = int(lengths.sum()) * K * 2
+    for budget in (table // 16, table // 64, 10 * 2 * K):
+        extra = ws(budget) - base
+        assert 0 < extra <= budget + 4096, (budget, extra)
