@@ -182,6 +182,49 @@ def per_sequence_comparator(fv, m, lengths, E, K, n_sample, device):
             "ms": ms}
 
 
+def config3_dense(fv, T, device, lib):
+    """K=4096 dense (Dirichlet 0.1 rows), batch 8 of length T: vanilla with
+    the full backpointer table against FLASH P=16 under a backpointer budget
+    of 1/16 of that table (budget leaves)."""
+    import torch
+
+    import workloads as W
+    K, n = 4096, 8
+    log_pi, logA = W.config3_dense_model()
+    m = fv.Model(log_pi, logA, device=device)
+    E = W.gaussian_emissions_packed_device(n * T, K, seed=3, device=device, chunk_rows=1 << 16)
+    b = fv.Batch([T] * n, E=E.view(-1), models=[m], device=device)
+    table = n * T * K * 2
+    out = {"workload": f"K={K} dense (Dirichlet 0.1 rows), batch {n}, T={T}, E = log_softmax N(0,1)",
+           "state_steps": n * T * K}
+    res = {}
+    for name, kw in (("vanilla", {"mode": "vanilla"}),
+                     ("flash_P16_budget_1_16", {"mode": "flash", "P": 16, "mem_budget": table // 16})):
+        d = fv.Decoder([m], b, **kw)
+        d(check=True)
+        ms, fwd = time_decoder(d, 1, 0, lib)
+        res[name] = d
+        out[name] = {"ms": ms, "value": n * T * K / (ms / 1e3), "unit": UNIT, "workspace_bytes": d.ws_bytes,
+                     "forward_kernels_ms": fwd}
+    pv, sv = res["vanilla"].paths, res["vanilla"].scores
+    pf, sf = res["flash_P16_budget_1_16"].paths, res["flash_P16_budget_1_16"].scores
+    out["flash_P16_budget_1_16"]["bit_identical_to_vanilla"] = bool(
+        torch.equal(pv, pf) and torch.equal(sv.view(torch.int32), sf.view(torch.int32)))
+    out["flash_P16_budget_1_16"]["time_vs_vanilla"] = out["flash_P16_budget_1_16"]["ms"] / out["vanilla"]["ms"]
+    out["flash_P16_budget_1_16"]["leaf_budget_bytes"] = table // 16
+    out["full_backpointer_table_bytes"] = table
+    cells = n * (T - 1) * K * K
+    pk, _ = peaks()
+    peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
+    fwd = out["vanilla"]["forward_kernels_ms"]
+    achieved = 2.0 * cells / (fwd / 1e3) / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": "wide_fwd_kernel", "achieved": achieved, "peak": peak,
+                       "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": fwd, "cells": cells}
+    del res, E
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_run(seconds, rate=2000.0, n_streams=128, max_wall=30.0):
     """Serving loop: Poisson arrivals, mixed K and T, exact and beam B=256,
     admitted under a 40 GB device-memory budget.  Admission stops after
@@ -330,6 +373,19 @@ def run_ours(args):
             modes[f"flash_P{P}"]["bit_identical_to_vanilla"] = bool(
                 torch.equal(pv_, pf_) and torch.equal(sv_.view(torch.int32), sf_.view(torch.int32)))
             del dflash
+        # budget leaves: FLASH P=16 whose leaf backpointers fit 1/16 of the
+        # full table
+        table = int(lengths.astype(np.int64).sum()) * K * 2
+        db = fv.Decoder([m], batch, mode="flash", P=16, mem_budget=table // 16)
+        db(check=True)
+        bms, _ = time_decoder(db, max(2, args.steps // 20), 2, lib)
+        modes["flash_P16_budget_1_16"] = {
+            "value": state_steps / (bms / 1e3), "unit": UNIT, "ms_per_step": bms, "time_vs_vanilla": bms / ms,
+            "bit_identical_to_vanilla": bool(torch.equal(dec.paths, db.paths) and torch.equal(
+                dec.scores.view(torch.int32), db.scores.view(torch.int32))),
+            "workspace_bytes": db.ws_bytes, "vanilla_workspace_bytes": dec.ws_bytes,
+            "full_backpointer_table_bytes": table, "leaf_budget_bytes": table // 16}
+        del db
         comp = per_sequence_comparator(fv, m, lengths, wl["E"], K, 32, device)
         comp["batched_over_per_sequence"] = value / world / comp["value"]
         modes["plain_per_sequence_gpu"] = comp
@@ -359,6 +415,8 @@ def run_ours(args):
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
     if modes:
         out["modes"] = modes
+    if rank == 0 and args.c3_T > 0:
+        out["config3_dense"] = config3_dense(fv, args.c3_T, device, lib)
     if rank == 0 and args.serve_seconds > 0:
         out["serving"] = serving_run(args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -383,6 +441,8 @@ def main():
     ap.add_argument("--K", type=int, default=256, help="states (the default workload has K=256)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FLASH and per-sequence rows")
+    ap.add_argument("--c3-T", dest="c3_T", type=int, default=100000,
+                    help="length of the K=4096 batch-8 run (0 = skip)")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=2.0,
                     help="arrival window of the serving run (60 = the full serving workload; 0 = skip)")
     args = ap.parse_args()
