@@ -225,6 +225,32 @@ def config3_dense(fv, T, device, lib):
     return out
 
 
+def config3_sparse(fv, T, device, lib):
+    """K=65536 CSR (32 successors per state), batch 8 of length T: dynamic
+    beam search with B in {128, 512, 2048}."""
+    import torch
+
+    import workloads as W
+    K, n = 65536, 8
+    log_pi, rp, col, val = W.config3_sparse_model()
+    m = fv.Model(log_pi, row_ptr=rp, col=col, val=val, device=device)
+    E = W.gaussian_emissions_packed_device(n * T, K, seed=4, device=device, chunk_rows=1 << 13)
+    b = fv.Batch([T] * n, E=E.view(-1), models=[m], device=device)
+    out = {"workload": f"K={K} CSR (32 successors, Dirichlet 1 weights), batch {n}, T={T} "
+                       f"(T-prefix of the 100 000-step sequences), E = log_softmax N(0,1)"}
+    for B in (128, 512, 2048):
+        d = fv.Decoder([m], b, mode="beam", B=B, P=0)
+        d(check=True)
+        ms, fwd = time_decoder(d, 1, 0, lib)
+        out[f"beam_B{B}"] = {"ms": ms, "value": n * T * K / (ms / 1e3), "unit": UNIT,
+                             "edge_relaxations_per_s": n * (T - 1) * B * 32 / (ms / 1e3),
+                             "workspace_bytes": d.ws_bytes}
+        del d
+    del E
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_run(seconds, rate=2000.0, n_streams=128, max_wall=30.0):
     """Serving loop: Poisson arrivals, mixed K and T, exact and beam B=256,
     admitted under a 40 GB device-memory budget.  Admission stops after
@@ -417,6 +443,8 @@ def run_ours(args):
         out["modes"] = modes
     if rank == 0 and args.c3_T > 0:
         out["config3_dense"] = config3_dense(fv, args.c3_T, device, lib)
+    if rank == 0 and args.c3s_T > 0:
+        out["config3_sparse"] = config3_sparse(fv, args.c3s_T, device, lib)
     if rank == 0 and args.serve_seconds > 0:
         out["serving"] = serving_run(args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -443,6 +471,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FLASH and per-sequence rows")
     ap.add_argument("--c3-T", dest="c3_T", type=int, default=100000,
                     help="length of the K=4096 batch-8 run (0 = skip)")
+    ap.add_argument("--c3s-T", dest="c3s_T", type=int, default=2000,
+                    help="length of the K=65536 sparse beam runs (0 = skip)")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=2.0,
                     help="arrival window of the serving run (60 = the full serving workload; 0 = skip)")
     args = ap.parse_args()
