@@ -109,9 +109,22 @@ typedef struct {
 
 /* mode and its knobs: P = parallelism degree of the first split (Sec.
  * V-A.3; P < 2 means the binary root of Alg. 2), B = beam width (Sec. V-C;
- * B >= K keeps every finite state), mem_budget_bytes = FLASH working
- * memory the decoder may use for per-segment backpointer tables (0 = pure
- * divide and conquer). */
+ * B >= K keeps every finite state).
+ *
+ * mem_budget_bytes (FV_FLASH only): bytes of per-segment backpointer
+ * tables the decoder may hold at once.  The first task level of Alg. 1
+ * whose every task (m, n) fits -- (n - m) rows of K uint16 -- is solved
+ * directly instead of being split further: the pruned start of Sec. V-B.2,
+ * the recursion of Sec. III-A keeping psi_{m+1..n}, and the backtrack from
+ * the known q*_n.  Those tasks run in waves whose tables fit the budget;
+ * results are unchanged.  0 = pure divide and conquer.  The workspace grows
+ * by at most the budget plus a small wave table.
+ *
+ * Supported: FV_VANILLA and FV_FLASH need dense transitions with
+ * K <= 4096 (FV_EUNSUPPORTED otherwise); K > 1024 runs one cooperative
+ * launch over the whole GPU whose device waits are bounded (FV_ETIMEOUT in
+ * the status word if one runs out).  FV_BEAM takes dense or CSR
+ * transitions with K <= 65536. */
 typedef struct {
   int32_t mode;               /* fv_mode                         */
   int32_t P;
