@@ -33,6 +33,12 @@ UNIT = "state-steps/s"
 WORKLOAD = "batched-uneven: 1024 seqs, K=256 dense FP32, T~U[500,4000], E=log_softmax(N(0,1))"
 
 
+# DRAM bytes per state-step of dense_fwd_kernel (K=256, vanilla): reads of
+# E plus writes of psi, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of a 128-sequence launch of this workload.
+DRAM_BYTES_PER_STATE_STEP = (279012864 + 110379776) / (271316 * 256)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -433,7 +439,12 @@ def run_ours(args):
            "clocks": clocks,
            "gpu_launches": launches,
            "roofline": {"bound": "alu", "kernel": "dense_fwd_kernel", "achieved": achieved,
-                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "traffic": (DRAM_BYTES_PER_STATE_STEP * state_steps
+                                    if (args.K == 256 and args.mode == "vanilla") else None),
+                        "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of "
+                                        "this kernel on 128 sequences (5.61 B per state-step), scaled to this "
+                                        "launch's state-steps",
                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 ops x %.0f MHz (max clock)" % pk.get(
                             "sm_max_mhz", 2070.0),
                         "ops_per_cell": 2, "cells_per_launch": cells, "kernel_ms": fwd_ms},
