@@ -15,7 +15,9 @@
 //  * c_j = fl(M_j + E_t[j]); exact top-B: 4-pass MSB radix select on the
 //    order-preserving 32-bit key (-0 folded into +0), then the keys equal
 //    to the threshold are taken lowest id first (block scan in id order).
-// Beams, candidates and keys live in a per-CTA slice of the workspace.
+// Beams and candidates live in shared memory when they fit (they are
+// re-read several times per step), else in a per-CTA slice of the
+// workspace; CSR scatter keys always live in the workspace.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -33,6 +35,11 @@ __device__ inline uint32_t ord_key(float x) {
   uint32_t u = __float_as_uint(x);
   if (u == 0x80000000u) u = 0u;
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Inverse of ord_key (zero comes back as +0).
+__device__ inline float ord_value(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
 __device__ inline int block_sum(int v, int* red) {
@@ -115,7 +122,10 @@ struct BeamScratch {
   float* snap_val;           // [Bcap]
 };
 
-__device__ inline BeamScratch beam_scratch(const BeamArgs& a) {
+// Shared-memory words of the touched bitmap, rounded to 16 bytes.
+__host__ __device__ inline size_t beam_bitmap_words(int K) { return (size_t)(((K + 31) / 32 + 3) / 4 * 4); }
+
+__device__ inline BeamScratch beam_scratch(const BeamArgs& a, uint32_t* smem) {
   BeamScratch s;
   char* base = reinterpret_cast<char*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride;
   const size_t K = (size_t)a.K, B = (size_t)a.Bcap;
@@ -138,6 +148,29 @@ __device__ inline BeamScratch beam_scratch(const BeamArgs& a) {
   s.snap_id = reinterpret_cast<int32_t*>(base);
   base += align_up(B * 4);
   s.snap_val = reinterpret_cast<float*>(base);
+  // shared-memory homes (after the bitmap): beams, then candidates
+  uint32_t* sp = smem + beam_bitmap_words(a.K);
+  if (a.beam_smem) {
+    for (int p = 0; p < 2; ++p) {
+      s.id[p] = reinterpret_cast<int32_t*>(sp);
+      sp += B;
+      s.val[p] = reinterpret_cast<float*>(sp);
+      sp += B;
+      s.mid[p] = reinterpret_cast<int32_t*>(sp);
+      sp += B;
+      s.src[p] = reinterpret_cast<int32_t*>(sp);
+      sp += B;
+    }
+    s.snap_id = reinterpret_cast<int32_t*>(sp);
+    sp += B;
+    s.snap_val = reinterpret_cast<float*>(sp);
+    sp += B;
+  }
+  if (a.cand_smem) {
+    s.cval = reinterpret_cast<float*>(sp);
+    sp += K;
+    s.cslot = reinterpret_cast<int32_t*>(sp);
+  }
   return s;
 }
 
@@ -153,20 +186,34 @@ struct BeamSmem {
   int* misc;          // [8]
 };
 
-// Top-B of the touched candidates (finite only) -> beam buffer p, in id
-// order.  Returns the beam size (identical in every thread).
-__device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid) {
-  const int K = a.K, nw = (K + 31) >> 5, tid = threadIdx.x;
-  // count finite touched candidates
-  int cnt = 0;
-  for (int w = tid; w < nw; w += blockDim.x) {
-    uint32_t bits = sm.touched[w];
+// Calls f(j) for every touched target j of this thread's contiguous range
+// [j0, j1) of the state ids, in ascending j.
+template <class F>
+__device__ inline void for_touched(const BeamSmem& sm, int j0, int j1, F&& f) {
+  for (int j = j0; j < j1;) {
+    const int w = j >> 5, wend = min(j1, (w + 1) << 5);
+    const int lo = j & 31, hi = wend - (w << 5);
+    uint32_t bits = sm.touched[w] & (0xffffffffu << lo);
+    if (hi < 32) bits &= (1u << hi) - 1u;
     while (bits) {
-      const int j = (w << 5) + __ffs(bits) - 1;
+      const int jj = (w << 5) + __ffs(bits) - 1;
       bits &= bits - 1;
-      if (isfinite(S.cval[j])) ++cnt;
+      f(jj);
     }
+    j = wend;
   }
+}
+
+// Top-B of the touched candidates (finite only) -> beam buffer p, in id
+// order.  Returns the beam size (identical in every thread).  Each thread
+// owns a contiguous range of state ids, so the final compaction in thread
+// order is id order.
+__device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid) {
+  const int K = a.K, tid = threadIdx.x, lane = tid & 31;
+  const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int j0 = min(K, tid * per), j1 = min(K, j0 + per);
+  int cnt = 0;
+  for_touched(sm, j0, j1, [&](int j) { cnt += isfinite(S.cval[j]) ? 1 : 0; });
   const int n_fin = block_sum(cnt, sm.red);
   uint32_t thr = 0u;
   int need_eq = 0;
@@ -177,26 +224,39 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
     for (int shift = 24; shift >= 0; shift -= 8) {
       for (int k = tid; k < 256; k += blockDim.x) sm.hist[k] = 0;
       __syncthreads();
-      for (int w = tid; w < nw; w += blockDim.x) {
-        uint32_t bits = sm.touched[w];
-        while (bits) {
-          const int j = (w << 5) + __ffs(bits) - 1;
-          bits &= bits - 1;
-          const float c = S.cval[j];
-          if (!isfinite(c)) continue;
-          const uint32_t u = ord_key(c);
-          if ((u & mask) == prefix) atomicAdd(&sm.hist[(u >> shift) & 0xFFu], 1);
-        }
-      }
+      for_touched(sm, j0, j1, [&](int j) {
+        const float c = S.cval[j];
+        if (!isfinite(c)) return;
+        const uint32_t u = ord_key(c);
+        if ((u & mask) == prefix) atomicAdd(&sm.hist[(u >> shift) & 0xFFu], 1);
+      });
       __syncthreads();
-      if (tid == 0) {
-        int acc = 0, d = 255;
-        for (; d > 0; --d) {
-          if (acc + sm.hist[d] >= remaining) break;
-          acc += sm.hist[d];
+      // the digit where the count from the top reaches `remaining`: lane l
+      // holds digits 255-8l .. 248-8l, a warp scan finds the lane, the lane
+      // its digit
+      if (tid < 32) {
+        int h[8], sum = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          h[u] = sm.hist[255 - 8 * lane - u];
+          sum += h[u];
         }
-        sm.misc[0] = d;
-        sm.misc[1] = remaining - acc;
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int excl = incl - sum;
+        if (excl < remaining && remaining <= incl) {
+          int acc = excl, d = 255 - 8 * lane - 7;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (acc + h[u] >= remaining) { d = 255 - 8 * lane - u; break; }
+            acc += h[u];
+          }
+          sm.misc[0] = d;
+          sm.misc[1] = remaining - acc;
+        }
       }
       __syncthreads();
       prefix |= (uint32_t)sm.misc[0] << shift;
@@ -207,52 +267,39 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
     thr = prefix;
     need_eq = remaining;  // keys == thr to take, lowest ids first
   }
-  // selection in id order: each thread owns a contiguous block of words
-  const int per = (nw + blockDim.x - 1) / blockDim.x;
-  const int w0 = tid * per, w1 = min(nw, w0 + per);
   int n_gt = 0, n_eq = 0;
-  for (int w = w0; w < w1; ++w) {
-    uint32_t bits = sm.touched[w];
-    while (bits) {
-      const int j = (w << 5) + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const float c = S.cval[j];
-      if (!isfinite(c)) continue;
-      if (all) { ++n_gt; continue; }
-      const uint32_t u = ord_key(c);
-      if (u > thr) ++n_gt;
-      else if (u == thr) ++n_eq;
-    }
-  }
+  for_touched(sm, j0, j1, [&](int j) {
+    const float c = S.cval[j];
+    if (!isfinite(c)) return;
+    if (all) { ++n_gt; return; }
+    const uint32_t u = ord_key(c);
+    if (u > thr) ++n_gt;
+    else if (u == thr) ++n_eq;
+  });
   int tot_eq, tot;
   const int eq_before = block_scan(n_eq, sm.red, &tot_eq);
-  int take_eq = min(max(need_eq - eq_before, 0), n_eq);
+  const int take_eq = min(max(need_eq - eq_before, 0), n_eq);
   const int pos = block_scan(n_gt + take_eq, sm.red, &tot);
   int o = pos, eq_seen = 0;
-  for (int w = w0; w < w1; ++w) {
-    uint32_t bits = sm.touched[w];
-    while (bits) {
-      const int j = (w << 5) + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const float c = S.cval[j];
-      if (!isfinite(c)) continue;
-      bool take = all;
-      if (!all) {
-        const uint32_t u = ord_key(c);
-        if (u > thr) take = true;
-        else if (u == thr) take = (eq_seen++ < take_eq);
-      }
-      if (!take) continue;
-      const int sl = S.cslot[j];
-      S.id[p][o] = j;
-      S.val[p][o] = c;
-      S.src[p][o] = sl;
-      if (need_mid == 1) S.mid[p][o] = S.id[p ^ 1][sl];
-      else if (need_mid == 2) S.mid[p][o] = S.mid[p ^ 1][sl];
-      else S.mid[p][o] = -1;
-      ++o;
+  for_touched(sm, j0, j1, [&](int j) {
+    const float c = S.cval[j];
+    if (!isfinite(c)) return;
+    bool take = all;
+    if (!all) {
+      const uint32_t u = ord_key(c);
+      if (u > thr) take = true;
+      else if (u == thr) take = (eq_seen++ < take_eq);
     }
-  }
+    if (!take) return;
+    const int sl = S.cslot[j];
+    S.id[p][o] = j;
+    S.val[p][o] = c;
+    S.src[p][o] = sl;
+    if (need_mid == 1) S.mid[p][o] = S.id[p ^ 1][sl];
+    else if (need_mid == 2) S.mid[p][o] = S.mid[p ^ 1][sl];
+    else S.mid[p][o] = -1;
+    ++o;
+  });
   __syncthreads();
   return tot;
 }
@@ -260,17 +307,13 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
 // Clear the touched bitmap (and CSR keys of touched targets).
 __device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm) {
   const int nw = (a.K + 31) >> 5;
-  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-    uint32_t bits = sm.touched[w];
-    if (a.trans != FV_TRANS_DENSE) {
-      while (bits) {
-        const int j = (w << 5) + __ffs(bits) - 1;
-        bits &= bits - 1;
-        S.keys[j] = 0ull;
-      }
-    }
-    sm.touched[w] = 0u;
+  if (a.trans != FV_TRANS_DENSE) {
+    const int per = (a.K + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = min(a.K, (int)threadIdx.x * per), j1 = min(a.K, j0 + per);
+    for_touched(sm, j0, j1, [&](int j) { S.keys[j] = 0ull; });
+    __syncthreads();
   }
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) sm.touched[w] = 0u;
   __syncthreads();
 }
 
@@ -278,16 +321,43 @@ __device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamS
 __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int p, int nb, int t) {
   const int K = a.K;
   if (a.trans == FV_TRANS_DENSE) {
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    // G threads per target (adjacent lanes) split the beam by slot
+    // residue; the group keeps the highest value, the lowest slot on ties
+    int G = 1;
+    while (G < 32 && 2 * G * K <= (int)blockDim.x) G *= 2;
+    const int groups = (int)blockDim.x / G, sub = (int)threadIdx.x % G;
+    for (int base = 0; base < K; base += groups) {
+      const int j = base + (int)threadIdx.x / G;
       float best = -CUDART_INF_F;
       int sl = -1;
-      for (int k = 0; k < nb; ++k) {
-        const float c = __fadd_rn(S.val[p][k], __ldg(a.logA + (int64_t)S.id[p][k] * K + j));
-        if (sl < 0 || c > best) { best = c; sl = k; }
+      if (j < K) {
+        // eight sources in flight per round; compared in slot order
+        int k = sub;
+        for (; k + 7 * G < nb; k += 8 * G) {
+          float w[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) w[u] = __ldg(a.logA + (int64_t)S.id[p][k + u * G] * K + j);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float c = __fadd_rn(S.val[p][k + u * G], w[u]);
+            if (sl < 0 || c > best) { best = c; sl = k + u * G; }
+          }
+        }
+        for (; k < nb; k += G) {
+          const float c = __fadd_rn(S.val[p][k], __ldg(a.logA + (int64_t)S.id[p][k] * K + j));
+          if (sl < 0 || c > best) { best = c; sl = k; }
+        }
       }
-      S.cslot[j] = sl;
-      S.cval[j] = __fadd_rn(best, beam_emit(a, jb, t, j));
-      if (sl >= 0) atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+      for (int o = 1; o < G; o <<= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o, G);
+        const int os = __shfl_xor_sync(0xffffffffu, sl, o, G);
+        if (os >= 0 && (sl < 0 || ov > best || (ov == best && os < sl))) { best = ov; sl = os; }
+      }
+      if (sub == 0 && j < K) {
+        S.cslot[j] = sl;
+        S.cval[j] = __fadd_rn(best, beam_emit(a, jb, t, j));
+        if (sl >= 0) atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+      }
     }
     __syncthreads();
     return;
@@ -306,18 +376,18 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
     }
   }
   __syncthreads();
-  const int nw = (K + 31) >> 5;
-  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-    uint32_t bits = sm.touched[w];
-    while (bits) {
-      const int j = (w << 5) + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const int sl = (int)(0xFFFFFFFFull - (S.keys[j] & 0xFFFFFFFFull));
-      const float m = __fadd_rn(S.val[p][sl], beam_csr_w(a, S.id[p][sl], j));
-      S.cslot[j] = sl;
-      S.cval[j] = __fadd_rn(m, beam_emit(a, jb, t, j));
-    }
-  }
+  const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
+  for_touched(sm, j0, j1, [&](int j) {
+    const unsigned long long key = S.keys[j];
+    const int sl = (int)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+    // the winning candidate is the key's value (the order map is a
+    // bijection away from zero); a zero is recomputed for its sign
+    float m = ord_value((uint32_t)(key >> 32));
+    if (m == 0.0f) m = __fadd_rn(S.val[p][sl], beam_csr_w(a, S.id[p][sl], j));
+    S.cslot[j] = sl;
+    S.cval[j] = __fadd_rn(m, beam_emit(a, jb, t, j));
+  });
   __syncthreads();
 }
 
@@ -405,7 +475,7 @@ __global__ void __launch_bounds__(kBeamThreads, 1) beam_kernel(BeamArgs a) {
   sm.hist = hist;
   sm.misc = misc;
   if (a.hdr->status != 0) return;
-  BeamScratch S = beam_scratch(a);
+  BeamScratch S = beam_scratch(a, bsm);
   const int K = a.K, nw = (K + 31) >> 5;
   for (int w = threadIdx.x; w < nw; w += blockDim.x) sm.touched[w] = 0u;
   if (a.trans != FV_TRANS_DENSE)
@@ -595,12 +665,19 @@ cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = sizeof(uint32_t) * (size_t)((a.K + 31) / 32);
+  BeamArgs b = a;
+  size_t smem = sizeof(uint32_t) * beam_bitmap_words(a.K);
+  const size_t beam_bytes = sizeof(int32_t) * 10 * (size_t)a.Bcap;
+  const size_t cand_bytes = sizeof(int32_t) * 2 * (size_t)a.K;
+  b.beam_smem = smem + beam_bytes <= (size_t)160 * 1024;
+  if (b.beam_smem) smem += beam_bytes;
+  b.cand_smem = smem + cand_bytes <= (size_t)208 * 1024;
+  if (b.cand_smem) smem += cand_bytes;
   cudaError_t e = cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = max_jobs < a.max_ctas ? max_jobs : a.max_ctas;
   if (grid < 1) return cudaSuccess;
-  beam_kernel<<<grid, kBeamThreads, smem, st>>>(a);
+  beam_kernel<<<grid, kBeamThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -129,6 +129,8 @@ struct BeamArgs {
   int32_t* div_n;             // root: per sequence [pe_cap] beam sizes
   int64_t div_stride;         // pe_cap * Wcap
   int32_t pe_cap;
+  int32_t beam_smem;          // beams (both buffers + subtask snapshot) live in shared memory
+  int32_t cand_smem;          // candidate values / sources live in shared memory
   WsHeader* hdr;
 };
 
