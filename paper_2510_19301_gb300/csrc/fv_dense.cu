@@ -205,18 +205,26 @@ __host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
   return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
 }
 
-template <int J, int S, int NW, int CL, int KPM, bool STREAM>
+// TW = columns per lane (8, or 4 for the 16-warp configurations): a lane
+// holds 4 slots x TW columns; a warp covers all S slots and LJ*TW columns;
+// CG warps side by side cover the CTA's J columns and RG = NW/CG row groups
+// split the rows.
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8>
 struct DenseCfg {
   static constexpr int NT = NW * 32;
-  static constexpr int LJ = J / 8;
-  static constexpr int LS = 32 / LJ;
+  static constexpr int LS = S / 4;        // slot groups per warp
+  static constexpr int LJ = 32 / LS;      // column lanes per warp
+  static constexpr int WC = LJ * TW;      // columns per warp
+  static constexpr int CG = J / WC;       // column groups
+  static constexpr int RG = NW / CG;      // row groups
   static constexpr int OPT = S * J / NT;
   static constexpr int KP = KPM;          // rows, padded (-inf) to a fixed count
-  static constexpr int C = KPM / NW;      // rows per warp
+  static constexpr int C = KPM / RG;      // rows per row group
   static constexpr int CH = STREAM ? 32 : C;  // rows per argmax chunk
   static constexpr int NST = KPM <= 512 ? 8 : 5;  // streamed: ring stages of 4 rows per warp
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
-  static_assert(LJ * LS == 32 && LS * 4 == S, "lane tile is 4 sequences x 8 columns");
+  static_assert(LJ * LS == 32 && LS * 4 == S && (TW == 8 || TW == 4), "lane tile is 4 sequences x TW columns");
+  static_assert(J % WC == 0 && NW % CG == 0 && (!STREAM || (TW == 8 && CG == 1)), "warp tiling");
   static_assert((S * J) % NT == 0 && NT % J == 0, "epilogue: one column per thread, OPT slots");
   static_assert(C % CH == 0 && CH % 4 == 0 && (32 % CH == 0 || CH % 32 == 0), "chunks inside skew blocks");
   static_assert(!STREAM || C / CH <= 255 * 1, "chunk ids fit a byte");
@@ -225,14 +233,15 @@ struct DenseCfg {
   static constexpr size_t a_floats = STREAM ? (size_t)NW * NST * 4 * J : (size_t)KP * J;
   static constexpr size_t snap_floats = STREAM ? 0 : (size_t)S * KP;
   static constexpr size_t smem_bytes =
-      sizeof(float) * (a_floats + 2ull * S * KPS + (size_t)NW * S * J + snap_floats) +
-      sizeof(uint16_t) * 2ull * S * KP + (STREAM ? (size_t)NW * S * J : 0);
+      sizeof(float) * (a_floats + 2ull * S * KPS + (size_t)RG * S * J + snap_floats) +
+      sizeof(uint16_t) * 2ull * S * KP + (STREAM ? (size_t)RG * S * J : 0);
 };
 
-template <int J, int S, int NW, int CL, int KPM, bool STREAM>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW>
 __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW>;
   constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT, KP = Cfg::KP, C = Cfg::C, KPS = Cfg::KPS;
+  constexpr int CG = Cfg::CG, RG = Cfg::RG, WC = Cfg::WC;
   constexpr int CH = Cfg::CH, NST = Cfg::NST;
   extern __shared__ __align__(16) float smem[];
   __shared__ Slot slots[S];
@@ -244,10 +253,10 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   // with cp.async from the row-pair copy a.Ap in global memory
   float* sA = smem;                           // resident [KP/2][J] / streamed [NW][NST][2][J] float2
   float* sD = sA + Cfg::a_floats;             // [2][S][KPS] delta per slot, skewed rows
-  float* sPart = sD + 2 * S * KPS;            // [NW][S][J]  per-warp partial maxima
-  float* sSnap = sPart + NW * S * J;          // resident [S][KP] sub: delta at t_mid
+  float* sPart = sD + 2 * S * KPS;            // [RG][S][J]  per-row-group partial maxima
+  float* sSnap = sPart + RG * S * J;          // resident [S][KP] sub: delta at t_mid
   uint16_t* sMid = reinterpret_cast<uint16_t*>(sSnap + Cfg::snap_floats);  // [2][S][KP] MidState
-  uint8_t* sPC = reinterpret_cast<uint8_t*>(sMid + 2 * S * KP);            // streamed [NW][S][J] chunk
+  uint8_t* sPC = reinterpret_cast<uint8_t*>(sMid + 2 * S * KP);            // streamed [RG][S][J] chunk
   const float2* sA2 = reinterpret_cast<const float2*>(sA);
   // streamed: global snapshot rows of this cluster's slots (sub jobs)
   float* gSnap = STREAM ? a.snap_scratch + (size_t)(blockIdx.x / CL) * S * KP : nullptr;
@@ -535,29 +544,30 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       }
     } else     {
       const int sg = lane / LJ, jg = lane % LJ;
-      float acc[4][8];
+      const int cg = warp % CG, rg = warp / CG;
+      float acc[4][TW];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = -CUDART_INF_F;
-      const int i0 = warp * C;
+        for (int y = 0; y < TW; ++y) acc[x][y] = -CUDART_INF_F;
+      const int i0 = rg * C;
       const float* dbase = sD + (cur * S + sg * 4) * KPS + i0 + ((i0 >> 5) << 2);
-      const float2* abase = sA2 + (i0 / 2) * J + 2 * jg;
+      const float2* abase = sA2 + (i0 / 2) * J + cg * WC + 2 * jg;
 #pragma unroll
       for (int ii = 0; ii < C; ii += 4) {
         ulonglong2 dq[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) dq[x] = *reinterpret_cast<const ulonglong2*>(dbase + x * KPS + ii);
-        ulonglong2 aq[2][4];
+        ulonglong2 aq[2][TW / 2];
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-          for (int g = 0; g < 4; ++g)
+          for (int g = 0; g < TW / 2; ++g)
             aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + (ii / 2 + pr) * J + 2 * LJ * g);
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
+          for (int g = 0; g < TW / 2; ++g) {
             fadd2_max3(acc[x][2 * g], dq[x].x, aq[0][g].x);
             fadd2_max3(acc[x][2 * g], dq[x].y, aq[1][g].x);
             fadd2_max3(acc[x][2 * g + 1], dq[x].x, aq[0][g].y);
@@ -566,9 +576,9 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       }
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        float* pp = sPart + (warp * S + sg * 4 + x) * J + 2 * jg;
+        float* pp = sPart + (rg * S + sg * 4 + x) * J + cg * WC + 2 * jg;
 #pragma unroll
-        for (int g = 0; g < 4; ++g)
+        for (int g = 0; g < TW / 2; ++g)
           *reinterpret_cast<float2*>(pp + 2 * LJ * g) = make_float2(acc[x][2 * g], acc[x][2 * g + 1]);
       }
     }
@@ -588,13 +598,13 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         const uint8_t* pc = sPC + s * J + jj;
         wb = pc[0];
 #pragma unroll
-        for (int w = 1; w < NW; ++w) {
+        for (int w = 1; w < RG; ++w) {
           const float v = pp[w * S * J];
           if (v > bv) { bv = v; wb = pc[w * S * J]; }
         }
       } else {
 #pragma unroll
-        for (int w = 1; w < NW; ++w) {
+        for (int w = 1; w < RG; ++w) {
           const float v = pp[w * S * J];
           if (v > bv) { bv = v; wb = w; }
         }
@@ -849,10 +859,10 @@ __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* o
 }
 
 // ------------------------------------------------------------ host launchers
-template <int J, int S, int NW, int CL, int KPM, bool STREAM>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8>
 static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t st) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW>;
   a.KP = KPM;
   const size_t smem = Cfg::smem_bytes;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -945,8 +955,8 @@ cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st
 cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st) {
   if (a.K > 1024) return launch_wide_forward(a, st);
   if (a.K <= 64) return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
-  if (a.K <= 128) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
-  if (a.K <= 256) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
+  if (a.K <= 128) return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
+  if (a.K <= 256) return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);
   if (a.K <= 512) return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
   return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);
 }
