@@ -67,6 +67,11 @@ typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
 /* fv_params.flags */
 #define FV_COMPLETE_PRUNING 0x1u /* offset-0 re-initialisation of Sec. V-B.2     */
 #define FV_NO_SORT 0x2u          /* keep batch order (skip longest-first order)  */
+/* Test hook for failure detection: the first CTA of the whole-GPU engine
+ * (dense K > 1024) never publishes its step count, so every bounded wait on
+ * it runs out (about one second); the call then reports FV_ETIMEOUT in the
+ * status word and the CUDA context stays usable.  No other effect. */
+#define FV_TEST_WITHHOLD_STEP 0x80000000u
 
 /* One HMM, lambda = (pi, A, B) of Sec. III. K <= 65536 (backpointers are
  * uint16).  Dense transitions: logA[i*K + j] = log A_ij, row = source state.

@@ -627,6 +627,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
     da.paths = paths_out;
     da.P = p->P;
     da.complete = (p->flags & FV_COMPLETE_PRUNING) ? 1 : 0;
+    da.wide_withhold = (p->flags & FV_TEST_WITHHOLD_STEP) ? 1 : 0;
     da.hdr = hdr;
     {
       int kpm = 0, cols = 0;

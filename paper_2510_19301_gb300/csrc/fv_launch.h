@@ -77,6 +77,7 @@ struct DenseArgs {
   uint16_t* wide_M;
   float* wide_X;
   uint32_t* wide_flags;
+  int32_t wide_withhold;      // test hook: CTA 0 never publishes its step count
   WsHeader* hdr;
 };
 

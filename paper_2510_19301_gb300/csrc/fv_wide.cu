@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
       a.wide_D[nxt * SK + (int64_t)os * KD + oj] = dval;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !(a.wide_withhold && blockIdx.x == 0)) {
       __threadfence();
       st_release_u32(a.wide_flags + (size_t)blockIdx.x * 8, tau + 1);
     }

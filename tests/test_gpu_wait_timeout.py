@@ -1,0 +1,40 @@
+"""Failure detection of the whole-GPU engine without a GPU fault: with the
+test hook FV_TEST_WITHHOLD_STEP one CTA never publishes its step count, so
+the bounded waits of every CTA that depends on it run out (about a second).
+The call must report FV_ETIMEOUT through the workspace status word, leave
+the CUDA context usable, and the next ordinary call must decode exactly."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_withheld_step_times_out_and_context_survives():
+    import paper_2510_19301_gb300 as fv
+    from paper_2510_19301_gb300 import _lib as L
+    fv._lib.load(build_if_missing=True)
+    rng = np.random.default_rng(77)
+    K = 1100
+    log_pi, logA = W.random_model(K, rng)
+    lengths = [5, 9, 3]
+    E_list = [W.gaussian_emissions(t, K, rng) for t in lengths]
+    m = fv.Model(log_pi, logA)
+    b = fv.Batch(lengths, E=torch.from_numpy(np.concatenate(E_list)).cuda(), models=[m])
+    dec = fv.Decoder([m], b, mode="vanilla", flags=L.FV_TEST_WITHHOLD_STEP)
+    dec.launch()
+    torch.cuda.synchronize()
+    assert dec.device_status() == L.FV_ETIMEOUT
+    # the context is intact: an ordinary decode right after is exact
+    paths, scores = fv.decode([m], b, mode="vanilla")
+    paths, scores = paths.cpu().numpy(), scores.cpu().numpy()
+    hmm = oracle.HMM(log_pi, logA)
+    off = 0
+    for i, e in enumerate(E_list):
+        p, s = oracle.viterbi(hmm, e)
+        assert np.array_equal(paths[off:off + lengths[i]], p)
+        assert np.float32(scores[i]).view(np.int32) == np.float32(s).view(np.int32)
+        off += lengths[i]
