@@ -43,6 +43,27 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_seed(rank):
+    """Each rank decodes its own batch (weak scaling): same shape, its own
+    seeded lengths and emission scores."""
+    return 2 + 7919 * rank
+
+
+def aggregate_ranks(ms, units, device="cpu"):
+    """Whole-job throughput over the ranks of the process group (if any):
+    the units all ranks processed divided by the slowest rank's time.
+    Returns (value per second, max ms, total units)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max, total = float(t.item()), float(u.item())
+    return total / (ms_max / 1e3), ms_max, total
+
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms during the timed region."""
 
@@ -112,8 +133,8 @@ def make_workload(args, rank, device):
     import workloads as W
     K = args.K
     log_pi, logA = W.config2_model(seed=2, K=K)
-    lengths = W.config2_lengths(seed=2 + 7919 * rank, n_seq=args.n_seq)
-    E = W.gaussian_emissions_packed_device(int(lengths.sum()), K, seed=2 + 7919 * rank, device=device)
+    lengths = W.config2_lengths(seed=rank_seed(rank), n_seq=args.n_seq)
+    E = W.gaussian_emissions_packed_device(int(lengths.sum()), K, seed=rank_seed(rank), device=device)
     m = fv.Model(log_pi, logA, device=device)
     return dict(K=K, log_pi=log_pi, logA=logA, lengths=lengths, E=E, model=m)
 
@@ -362,11 +383,7 @@ def run_ours(args):
     status = dec.device_status()
     assert status == 0, f"device status {status}"
 
-    t_max = torch.tensor([ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    value = world * state_steps / (ms_max / 1e3)
+    value, ms_max, _ = aggregate_ranks(ms, state_steps, device=device)
 
     # end to end through the public API: pinned host E -> device, decode,
     # paths + scores -> pinned host, every step
@@ -389,6 +406,7 @@ def run_ours(args):
     f1.record(st)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    e2e_value, _, _ = aggregate_ranks(e2e_ms, state_steps, device=device)
     h2d = E_host.numel() * 4
     d2h = P_host.numel() * 4 + S_host.numel() * 4
 
@@ -448,7 +466,7 @@ def run_ours(args):
                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 ops x %.0f MHz (max clock)" % pk.get(
                             "sm_max_mhz", 2070.0),
                         "ops_per_cell": 2, "cells_per_launch": cells, "kernel_ms": fwd_ms},
-           "e2e": {"value": world * state_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
     if modes:
         out["modes"] = modes
