@@ -13,7 +13,7 @@
  * fix a float width; the GPU path computes in FP32 and must match this file to
  * 0 ulp, so this file computes in FP32 in the fixed order stated below.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  R1  Emission scores are added outside the max:
  *        delta_t[j] = fl( max_i fl(delta_{t-1}[i] + logA[i][j]) + E_t[j] ).
  *  R2  Every argmax takes the lowest index; the value kept is the winning
