@@ -385,30 +385,48 @@ def run_ours(args):
 
     value, ms_max, _ = aggregate_ranks(ms, state_steps, device=device)
 
-    # end to end through the public API: pinned host E -> device, decode,
-    # paths + scores -> pinned host, every step
+    # end to end through the public API: every step copies its emission
+    # scores from pinned host memory to the device, decodes them and reads
+    # paths + scores back to pinned host memory.  Two device input buffers
+    # (two Decoders) let the copy for step i+1 run on a copy stream while
+    # step i decodes.
     E_host = torch.empty(wl["E"].numel(), dtype=torch.float32, pin_memory=True)
     E_host.copy_(wl["E"].view(-1))
-    P_host = torch.empty(dec.paths.numel(), dtype=torch.int32, pin_memory=True)
-    S_host = torch.empty(dec.scores.numel(), dtype=torch.float32, pin_memory=True)
-    Edev = batch.E
+    E_dev = [batch.E, torch.empty_like(batch.E)]
+    batch2 = fv.Batch(lengths, E=E_dev[1], models=[m], device=device)
+    decs = [dec, fv.Decoder([m], batch2, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)]
+    P_host = [torch.empty(dec.paths.numel(), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    S_host = [torch.empty(dec.scores.numel(), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    copy_st = torch.cuda.Stream(device=device)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 20))
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
     for it in range(1 + e2e_steps):
         if it == 1:
             torch.cuda.synchronize()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
             f0.record(st)
-        Edev.copy_(E_host, non_blocking=True)
-        dec.launch()
-        P_host.copy_(dec.paths, non_blocking=True)
-        S_host.copy_(dec.scores, non_blocking=True)
+            copy_st.wait_event(f0)
+        k = it % 2
+        copy_st.wait_event(consumed[k])  # the decode that last read this buffer is done
+        with torch.cuda.stream(copy_st):
+            E_dev[k].copy_(E_host, non_blocking=True)
+        copied[k].record(copy_st)
+        st.wait_event(copied[k])
+        decs[k].launch(st)
+        consumed[k].record(st)
+        P_host[k].copy_(decs[k].paths, non_blocking=True)
+        S_host[k].copy_(decs[k].scores, non_blocking=True)
     f1.record(st)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
     e2e_value, _, _ = aggregate_ranks(e2e_ms, state_steps, device=device)
     h2d = E_host.numel() * 4
-    d2h = P_host.numel() * 4 + S_host.numel() * 4
+    d2h = P_host[0].numel() * 4 + S_host[0].numel() * 4
+    assert decs[0].device_status() == 0 and decs[1].device_status() == 0
+    assert torch.equal(decs[0].paths, decs[1].paths)
+    del decs[1], batch2, E_dev[1]
 
     modes = {}
     if not args.quick:
@@ -467,6 +485,7 @@ def run_ours(args):
                             "sm_max_mhz", 2070.0),
                         "ops_per_cell": 2, "cells_per_launch": cells, "kernel_ms": fwd_ms},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "pipelining": "two device input buffers: the H2D copy of step i+1 overlaps the decode of step i",
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
     if modes:
         out["modes"] = modes
