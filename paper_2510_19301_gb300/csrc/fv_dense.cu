@@ -643,15 +643,33 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           }
         }
       } else {
+        // four rows per step; equal nonzero floats have equal bits, so only
+        // the row is tracked and a zero maximum is recomputed at that row
+        // for its sign
 #pragma unroll
-        for (int k = CH / 2 - 1; k >= 0; --k) {
+        for (int k4 = CH / 4 - 1; k4 >= 0; --k4) {
 #pragma unroll
           for (int r = 0; r < OPT; ++r) {
-            float c0, c1;
-            fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k),
-                  *reinterpret_cast<const unsigned long long*>(ar[r] + k * astr), c0, c1);
-            if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
-            if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+            const float4 d4 = *reinterpret_cast<const float4*>(dr[r] + 4 * k4);
+            const unsigned long long dlo =
+                ((unsigned long long)__float_as_uint(d4.y) << 32) | (unsigned long long)__float_as_uint(d4.x);
+            const unsigned long long dhi =
+                ((unsigned long long)__float_as_uint(d4.w) << 32) | (unsigned long long)__float_as_uint(d4.z);
+            float c0, c1, c2, c3;
+            fadd2(dhi, *reinterpret_cast<const unsigned long long*>(ar[r] + (2 * k4 + 1) * astr), c2, c3);
+            fadd2(dlo, *reinterpret_cast<const unsigned long long*>(ar[r] + (2 * k4) * astr), c0, c1);
+            if (c3 == best[r]) arg[r] = wbase[r] + 4 * k4 + 3;
+            if (c2 == best[r]) arg[r] = wbase[r] + 4 * k4 + 2;
+            if (c1 == best[r]) arg[r] = wbase[r] + 4 * k4 + 1;
+            if (c0 == best[r]) arg[r] = wbase[r] + 4 * k4;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < OPT; ++r) {
+          if (best[r] == 0.0f) {
+            const int o = arg[r] - wbase[r];
+            const float2 ap = ar[r][(o >> 1) * astr];
+            val[r] = __fadd_rn(dr[r][o], (o & 1) ? ap.y : ap.x);
           }
         }
       }
