@@ -125,11 +125,15 @@ typedef struct {
  * results are unchanged.  0 = pure divide and conquer.  The workspace grows
  * by at most the budget plus a small wave table.
  *
- * Supported: FV_VANILLA and FV_FLASH need dense transitions with
+ * Supported: FV_VANILLA and FV_FLASH on dense transitions need
  * K <= 4096 (FV_EUNSUPPORTED otherwise); K > 1024 runs one cooperative
  * launch over the whole GPU whose device waits are bounded (FV_ETIMEOUT in
  * the status word if one runs out).  FV_BEAM takes dense or CSR
- * transitions with K <= 65536. */
+ * transitions with K <= 65536.  A batch with a CSR model is decoded
+ * exactly by the beam of Sec. V-C with every state kept (B = K; FLASH
+ * becomes FLASH-BS with the same P), which gives the same paths and scores
+ * as the exact recursion; mem_budget_bytes does not apply there, and a
+ * sequence with no finite path is reported as FV_EINFEASIBLE. */
 typedef struct {
   int32_t mode;               /* fv_mode                         */
   int32_t P;

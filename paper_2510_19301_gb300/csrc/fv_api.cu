@@ -534,10 +534,34 @@ const char* fv_status_str(fv_status s) {
   return "unknown status";
 }
 
+// Exact decoding (vanilla / FLASH) of a batch with a CSR model runs the
+// beam engine with every state kept (B = K): the beam then holds every
+// finite state, so each step is the exact step of Sec. III-A (and FLASH-BS
+// the exact FLASH).  Returns the parameters actually run.
+fv_params exact_params(const fv_model* models, int32_t n_models, const fv_params* p) {
+  fv_params q = *p;
+  if (p->mode != FV_VANILLA && p->mode != FV_FLASH) return q;
+  int32_t kmax = 0;
+  bool csr = false;
+  for (int m = 0; m < n_models; ++m) {
+    kmax = std::max(kmax, models[m].K);
+    csr = csr || models[m].trans == FV_TRANS_CSR;
+  }
+  if (!csr) return q;
+  q.mode = FV_BEAM;
+  q.B = kmax;
+  q.P = p->mode == FV_FLASH ? p->P : 0;
+  q.mem_budget_bytes = 0;
+  return q;
+}
+
 size_t fv_workspace_size(const fv_model* models, int32_t n_models, const fv_batch* batch,
-                         const fv_params* p) {
-  if (!p || !batch || !batch->T_host) return 0;
+                         const fv_params* p_in) {
+  if (!p_in || !batch || !batch->T_host) return 0;
   if (check_common(models, n_models, batch) != FV_OK) return 0;
+  if (p_in->mode == FV_FLASH && p_in->P < 1) return 0;
+  const fv_params pq = exact_params(models, n_models, p_in);
+  const fv_params* p = &pq;
   if (p->mode == FV_FLASH || (p->mode == FV_BEAM && p->P >= 1)) {
     if (p->P < 1 || (p->mode == FV_BEAM && p->B < 1)) return 0;
     const FlashPlan fp = plan_flash(models, n_models, batch, p->P, p->mode == FV_FLASH ? p->mem_budget_bytes : 0,
@@ -548,13 +572,16 @@ size_t fv_workspace_size(const fv_model* models, int32_t n_models, const fv_batc
   return layout_for(models, n_models, batch, p->mode, nullptr, p->B).total;
 }
 
-fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p,
+fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p_in,
                     void* workspace, size_t ws_bytes, int32_t* paths_out, float* scores_out,
                     fv_stream_t stream_) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream_);
-  if (!p) return FV_EINVAL;
+  if (!p_in) return FV_EINVAL;
   fv_status s = check_common(models, n_models, batch);
   if (s != FV_OK) return s;
+  if (p_in->mode == FV_FLASH && p_in->P < 1) return FV_EINVAL;
+  const fv_params pq = exact_params(models, n_models, p_in);
+  const fv_params* p = &pq;
   if (!workspace || ws_bytes < 4096 || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1))) return FV_EINVAL;
   if (batch->n_seq > 0 && (!paths_out || !scores_out)) return FV_EINVAL;
   if (p->mode != FV_VANILLA && p->mode != FV_FLASH && p->mode != FV_BEAM) return FV_EINVAL;
