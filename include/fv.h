@@ -67,6 +67,12 @@ typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
 /* fv_params.flags */
 #define FV_COMPLETE_PRUNING 0x1u /* offset-0 re-initialisation of Sec. V-B.2     */
 #define FV_NO_SORT 0x2u          /* keep batch order (skip longest-first order)  */
+/* Check the inputs on the device before decoding: NaN or +inf in logpi,
+ * logA / CSR weights, logB or the batch's emission scores, or a malformed
+ * CSR graph (row_ptr not non-decreasing from 0 to nnz, a column outside
+ * [0, K)), records FV_EINVAL in the status word and nothing is decoded.
+ * Without this flag such inputs are undefined (-inf is always allowed). */
+#define FV_CHECKED 0x4u
 /* Test hook for failure detection: the first CTA of the whole-GPU engine
  * (dense K > 1024) never publishes its step count, so every bounded wait on
  * it runs out (about one second); the call then reports FV_ETIMEOUT in the

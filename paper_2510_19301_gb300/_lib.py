@@ -22,6 +22,7 @@ FV_TRANS_DENSE, FV_TRANS_CSR = 0, 1
 FV_EMIT_DENSE, FV_EMIT_DISCRETE = 0, 1
 FV_COMPLETE_PRUNING = 0x1
 FV_NO_SORT = 0x2
+FV_CHECKED = 0x4
 FV_TEST_WITHHOLD_STEP = 0x80000000
 
 P = ctypes.c_void_p

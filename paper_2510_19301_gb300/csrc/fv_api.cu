@@ -626,6 +626,9 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   pa.hdr = hdr;
   pa.aux_cap = p->mode == FV_VANILLA ? cap : L.aux_elems;
   if (launch_prep(pa, st) != cudaSuccess) return FV_ECUDA;
+  if (p->flags & FV_CHECKED)
+    for (int m = 0; m < n_models; ++m)
+      if (launch_check_inputs(models[m], m, jobs, n, batch->E, batch->obs, hdr, st) != cudaSuccess) return FV_ECUDA;
   if (launch_order(jobs, n, (p->flags & FV_NO_SORT) ? 1 : 0, order, st) != cudaSuccess) return FV_ECUDA;
 
   if (p->mode == FV_BEAM) return decode_beam(models, n_models, batch, p, ws, L, fp, R, paths_out, scores_out, st);

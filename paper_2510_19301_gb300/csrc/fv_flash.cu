@@ -325,6 +325,62 @@ cudaError_t launch_leaf_backtrack(const Task* tasks, const int32_t* wave_first, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ FV_CHECKED
+__device__ inline bool bad_score(float x) { return isnan(x) || (isinf(x) && x > 0.f); }
+
+__global__ void check_array_kernel(const float* x, int64_t n, uint32_t what, WsHeader* hdr) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (bad_score(x[i])) {
+      set_status(hdr, FV_EINVAL, what);
+      return;
+    }
+}
+
+__global__ void check_csr_kernel(const int32_t* row_ptr, const int32_t* col, int32_t K, int64_t nnz, uint32_t what,
+                                 WsHeader* hdr) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[K] != nnz)) set_status(hdr, FV_EINVAL, what);
+  for (int64_t i = i0; i < K; i += stride)
+    if (row_ptr[i + 1] < row_ptr[i]) set_status(hdr, FV_EINVAL, what);
+  for (int64_t e = i0; e < nnz; e += stride)
+    if ((unsigned)col[e] >= (unsigned)K) set_status(hdr, FV_EINVAL, what);
+}
+
+// Emission rows (dense) or symbols (discrete) of every sequence of one
+// model: CTA y takes sequence y, its threads stride over the T*K values.
+__global__ void check_emissions_kernel(const Job* jobs, int32_t b0, int32_t model, int32_t K, const float* E,
+                                       const int32_t* obs, int32_t V, WsHeader* hdr) {
+  const int b = b0 + blockIdx.y;
+  const Job jb = jobs[b];
+  if (jb.model != model) return;
+  const int64_t n = E ? (int64_t)jb.T * K : (int64_t)jb.T;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (E ? bad_score(E[jb.e_off + i]) : (unsigned)obs[jb.e_off + i] >= (unsigned)V) {
+      set_status(hdr, FV_EINVAL, 0xe0000000u | (uint32_t)b);
+      return;
+    }
+  }
+}
+
+cudaError_t launch_check_inputs(const fv_model& m, int32_t model, const Job* jobs, int32_t n_seq, const float* E,
+                                const int32_t* obs, WsHeader* hdr, cudaStream_t st) {
+  const uint32_t tag = 0xc0000000u | ((uint32_t)model << 8);
+  check_array_kernel<<<64, 256, 0, st>>>(m.log_pi, m.K, tag | 1u, hdr);
+  if (m.trans == FV_TRANS_DENSE) {
+    check_array_kernel<<<1024, 256, 0, st>>>(m.logA, (int64_t)m.K * m.K, tag | 2u, hdr);
+  } else {
+    check_array_kernel<<<1024, 256, 0, st>>>(m.val, m.nnz, tag | 3u, hdr);
+    check_csr_kernel<<<256, 256, 0, st>>>(m.row_ptr, m.col, m.K, m.nnz, tag | 4u, hdr);
+  }
+  if (m.emit == FV_EMIT_DISCRETE) check_array_kernel<<<256, 256, 0, st>>>(m.logB, (int64_t)m.K * m.V, tag | 5u, hdr);
+  for (int b0 = 0; b0 < n_seq; b0 += 65535) {
+    const int nb = n_seq - b0 < 65535 ? n_seq - b0 : 65535;
+    check_emissions_kernel<<<dim3(16, nb), 256, 0, st>>>(jobs, b0, model, m.K, m.emit == FV_EMIT_DENSE ? E : nullptr,
+                                                         obs, m.V, hdr);
+  }
+  return cudaGetLastError();
+}
+
 __global__ void reset_counter(unsigned long long* pop) { *pop = 0ull; }
 
 cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st) {

@@ -175,6 +175,11 @@ cudaError_t launch_level1_tasks(const Job* jobs, const int32_t* order, int32_t b
 cudaError_t launch_child_tasks(const Task* in, const int32_t* in_count, int32_t max_in, Task* out,
                                int32_t* out_count, ScanTmp tmp, unsigned long long* pop_reset, cudaStream_t st);
 cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st);
+// FV_CHECKED: scan one model's arrays, and the emission scores (dense) or
+// symbols (discrete) of the sequences decoded with it, for values the
+// decoder does not accept; records FV_EINVAL in the header.
+cudaError_t launch_check_inputs(const fv_model& m, int32_t model, const Job* jobs, int32_t n_seq, const float* E,
+                                const int32_t* obs, WsHeader* hdr, cudaStream_t st);
 // Budget leaves: greedy packing of a task list into waves whose backpointer
 // rows (n - m per task) fit budget_rows; writes each task's row offset into
 // Task::pad and the waves' [first, count) into wave_first / wave_count
