@@ -347,6 +347,9 @@ def run_ours(args):
     lengths = wl["lengths"]
     m = wl["model"]
     batch = fv.Batch(lengths, E=wl["E"].view(-1), models=[m], device=device)
+    # engine configuration for this K class picked by the autotuner on this
+    # very batch (all candidates give identical results)
+    chosen = fv.autotune([m], batch, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)
     dec = fv.Decoder([m], batch, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)
     lib = fv._lib.load()
     state_steps = int(lengths.astype(np.int64).sum()) * K
@@ -471,6 +474,7 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": wl_name, "mode": args.mode, "P": args.P, "B": args.B,
                       "n_seq": int(len(lengths)), "sum_T": int(lengths.sum()), "K": K,
+                      "engine_variant": int(chosen[0]),
                       "l2": "inputs larger than L2 (E is %.2f GB per step)" % (wl["E"].numel() * 4 / 1e9)},
            "clocks": clocks,
            "gpu_launches": launches,

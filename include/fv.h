@@ -73,6 +73,9 @@ typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
  * [0, K)), records FV_EINVAL in the status word and nothing is decoded.
  * Without this flag such inputs are undefined (-inf is always allowed). */
 #define FV_CHECKED 0x4u
+/* Run the default engine configuration instead of the one chosen by
+ * fv_autotune / fv_set_engine_variant. */
+#define FV_NO_TUNE 0x8u
 /* Test hook for failure detection: the first CTA of the whole-GPU engine
  * (dense K > 1024) never publishes its step count, so every bounded wait on
  * it runs out (about one second); the call then reports FV_ETIMEOUT in the
@@ -200,6 +203,26 @@ fv_status fv_path_score(const fv_model* models, int32_t n_models, const fv_batch
 fv_status fv_timing_enable(int32_t on);
 fv_status fv_timing_reset(void);
 fv_status fv_timing_read(float* total_ms, int32_t* n_pairs);
+
+/* Autotuning of the exact forward engine (not in the paper).  Dense exact
+ * decoding has, per class of K (<= 64, <= 128, <= 256), several engine
+ * configurations -- warps per CTA and columns per lane -- that compute the
+ * same values in the same order and differ only in speed.  fv_autotune
+ * decodes the given request once per candidate of every class present
+ * (one warm-up and two timed calls each, CUDA events on `stream`), keeps
+ * the fastest per class for every later fv_decode in this process, and
+ * writes the chosen variant of each model's class to chosen[m] (may be
+ * NULL).  Same arguments and outputs as fv_decode; it synchronises the
+ * stream, so it is not capturable.  Requests without tunable classes
+ * return FV_OK at once with chosen[] = 0.  Device errors are returned. */
+fv_status fv_autotune(const fv_model* models, int32_t n_models, const fv_batch* batch,
+                      const fv_params* params, void* workspace, size_t ws_bytes,
+                      int32_t* paths_out, float* scores_out, fv_stream_t stream,
+                      int32_t* chosen);
+
+/* Set the engine variant of K's class directly (0 = default); returns the
+ * number of variants of that class.  For tuning studies and tests. */
+int32_t fv_set_engine_variant(int32_t K, int32_t variant);
 
 /* Bytes of the static device scratch behind fv_decode_noalloc. */
 #define FV_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)

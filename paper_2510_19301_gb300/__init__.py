@@ -20,7 +20,7 @@ from . import _lib as L
 from ._lib import FVError
 
 __all__ = ["Model", "Batch", "Decoder", "decode", "path_score", "workspace_size", "backward",
-           "ViterbiScore", "FVError", "MODES"]
+           "ViterbiScore", "FVError", "MODES", "autotune", "set_engine_variant"]
 
 MODES = {"vanilla": L.FV_VANILLA, "flash": L.FV_FLASH, "beam": L.FV_BEAM}
 
@@ -208,6 +208,29 @@ class Decoder:
             if s != L.FV_OK:
                 raise FVError(s, "fv_decode (device)")
         return self.paths, self.scores
+
+
+def autotune(models, batch, mode="vanilla", P=1, B=0, mem_budget=0, flags=0, stream=None):
+    """Time every engine configuration of the K classes in this request and
+    keep the fastest for later decodes in this process (fv_autotune).
+    Returns the chosen variant per model."""
+    if isinstance(models, Model):
+        models = [models]
+    d = Decoder(models, batch, mode=mode, P=P, B=B, mem_budget=mem_budget, flags=flags)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    chosen = (ctypes.c_int32 * len(d.models))()
+    rc = d.lib.fv_autotune(d._arr, len(d.models), ctypes.byref(d._bs), ctypes.byref(d._ps), _ptr(d.workspace),
+                           d.workspace.numel(), _ptr(d.paths), _ptr(d.scores), ctypes.c_void_p(st.cuda_stream),
+                           chosen)
+    if rc != L.FV_OK:
+        raise FVError(rc, "fv_autotune")
+    return list(chosen)
+
+
+def set_engine_variant(K, variant):
+    """Force the engine variant of K's class (0 = default); returns the
+    number of variants of that class."""
+    return int(L.load().fv_set_engine_variant(int(K), int(variant)))
 
 
 def decode(models, batch, mode="vanilla", P=1, B=0, mem_budget=0, flags=0, stream=None, check=True):

@@ -23,6 +23,7 @@ FV_EMIT_DENSE, FV_EMIT_DISCRETE = 0, 1
 FV_COMPLETE_PRUNING = 0x1
 FV_NO_SORT = 0x2
 FV_CHECKED = 0x4
+FV_NO_TUNE = 0x8
 FV_TEST_WITHHOLD_STEP = 0x80000000
 
 P = ctypes.c_void_p
@@ -121,6 +122,10 @@ def load(build_if_missing: bool = False):
     lib.fv_timing_read.restype = ctypes.c_int
     lib.fv_decode_noalloc.argtypes = [MP, i32, BP, P, P, P]
     lib.fv_decode_noalloc.restype = ctypes.c_int
+    lib.fv_autotune.argtypes = [MP, i32, BP, PP, P, sz, P, P, P, P]
+    lib.fv_autotune.restype = ctypes.c_int
+    lib.fv_set_engine_variant.argtypes = [i32, i32]
+    lib.fv_set_engine_variant.restype = i32
     lib.fv_version.argtypes = []
     lib.fv_version.restype = ctypes.c_char_p
     _lib = lib

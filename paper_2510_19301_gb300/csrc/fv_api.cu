@@ -658,6 +658,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
     da.P = p->P;
     da.complete = (p->flags & FV_COMPLETE_PRUNING) ? 1 : 0;
     da.wide_withhold = (p->flags & FV_TEST_WITHHOLD_STEP) ? 1 : 0;
+    da.no_tune = (p->flags & FV_NO_TUNE) ? 1 : 0;
     da.hdr = hdr;
     {
       int kpm = 0, cols = 0;
@@ -831,6 +832,63 @@ fv_status fv_backward(const fv_model* models, int32_t n_models, const fv_batch* 
   if (launch_backward(jobs, n, K, paths, grad_scores, dlog_pi, dlogA, dE, max_T, hdr, st) != cudaSuccess)
     return FV_ECUDA;
   return FV_OK;
+}
+
+int32_t fv_set_engine_variant(int32_t K, int32_t variant) {
+  if (K < 1) return 0;
+  dense_set_variant(K, variant);
+  return dense_variants(K);
+}
+
+fv_status fv_autotune(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p,
+                      void* workspace, size_t ws_bytes, int32_t* paths_out, float* scores_out, fv_stream_t stream,
+                      int32_t* chosen) {
+  if (!p || !models || n_models < 1) return FV_EINVAL;
+  fv_status s = check_common(models, n_models, batch);
+  if (s != FV_OK) return s;
+  const fv_params q = exact_params(models, n_models, p);
+  std::vector<int32_t> reps;  // one K per tunable class present
+  if (q.mode != FV_BEAM) {
+    for (int m = 0; m < n_models; ++m) {
+      const int K = models[m].K;
+      if (dense_variants(K) < 2) continue;
+      bool seen = false;
+      for (int32_t r : reps) seen = seen || dense_k_class(r) == dense_k_class(K);
+      if (!seen) reps.push_back(K);
+    }
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  fv_params run = *p;
+  run.flags &= ~FV_NO_TUNE;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!reps.empty() && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) return FV_ECUDA;
+  for (int32_t K : reps) {
+    float best = 0.f;
+    int bv = 0;
+    for (int v = 0; v < dense_variants(K); ++v) {
+      dense_set_variant(K, v);
+      s = fv_decode(models, n_models, batch, &run, workspace, ws_bytes, paths_out, scores_out, stream);
+      if (s != FV_OK) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && s == FV_OK; ++r)
+        s = fv_decode(models, n_models, batch, &run, workspace, ws_bytes, paths_out, scores_out, stream);
+      cudaEventRecord(e1, st);
+      if (s != FV_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { s = FV_ECUDA; break; }
+      s = fv_last_device_status(workspace, stream);
+      if (s != FV_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (v == 0 || ms < best) { best = ms; bv = v; }
+    }
+    dense_set_variant(K, s == FV_OK ? bv : 0);
+    if (s != FV_OK) break;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (chosen)
+    for (int m = 0; m < n_models; ++m) chosen[m] = q.mode == FV_BEAM ? 0 : dense_get_variant(models[m].K);
+  return s;
 }
 
 fv_status fv_timing_enable(int32_t on) {

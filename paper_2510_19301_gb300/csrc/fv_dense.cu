@@ -970,11 +970,51 @@ cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st
 }
 
 // Rows padded to a multiple of 4 * NW for the chosen configuration.
+// Engine configurations per K class (variant 0 is the default).  Every
+// variant computes the same values in the same order, so the choice only
+// changes speed: warps per CTA and columns per lane (TW) for the resident
+// classes, ring depth for the streamed ones is fixed.
+int dense_k_class(int K) {
+  if (K <= 64) return 0;
+  if (K <= 128) return 1;
+  if (K <= 256) return 2;
+  if (K <= 512) return 3;
+  if (K <= 1024) return 4;
+  return 5;  // whole-GPU engine
+}
+int dense_variants(int K) {
+  switch (dense_k_class(K)) {
+    case 0: return 3;
+    case 1: return 2;
+    case 2: return 2;
+    default: return 1;
+  }
+}
+
+static int g_variant[6] = {0, 0, 0, 0, 0, 0};  // chosen by fv_autotune
+
+void dense_set_variant(int K, int v) {
+  const int c = dense_k_class(K);
+  g_variant[c] = (v >= 0 && v < dense_variants(K)) ? v : 0;
+}
+int dense_get_variant(int K) { return g_variant[dense_k_class(K)]; }
+
 cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st) {
   if (a.K > 1024) return launch_wide_forward(a, st);
-  if (a.K <= 64) return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
-  if (a.K <= 128) return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
-  if (a.K <= 256) return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);
+  const int v = a.no_tune ? 0 : g_variant[dense_k_class(a.K)];
+  if (a.K <= 64) {
+    if (v == 1) return launch_dense_cfg<64, 16, 8, 1, 64, false, 4>(a, max_clusters, st);
+    if (v == 2) return launch_dense_cfg<64, 16, 16, 1, 64, false, 4>(a, max_clusters, st);
+    return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
+  }
+  if (a.K <= 128) {
+    if (v == 1) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
+    return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
+  }
+  if (a.K <= 256) {
+    if (v == 1) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
+    return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);
+  }
   if (a.K <= 512) return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
   return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);
 }

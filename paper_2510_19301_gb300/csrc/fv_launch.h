@@ -78,6 +78,7 @@ struct DenseArgs {
   float* wide_X;
   uint32_t* wide_flags;
   int32_t wide_withhold;      // test hook: CTA 0 never publishes its step count
+  int32_t no_tune;            // use the default engine configuration, not the tuned one
   WsHeader* hdr;
 };
 
@@ -148,6 +149,11 @@ struct ScoreArgs {
 };
 
 int dense_supported_K(int K);
+// Engine configuration variants of a K class and the tuned choice.
+int dense_k_class(int K);
+int dense_variants(int K);
+void dense_set_variant(int K, int v);
+int dense_get_variant(int K);
 int device_sm_count();
 bool wide_geometry(int K, int nsm, WideGeom* g);
 size_t wide_scratch_bytes(int K, int nsm);
