@@ -247,6 +247,15 @@ def config3_dense(fv, T, device, lib):
     achieved = 2.0 * cells / (fwd / 1e3) / 1e12
     out["roofline"] = {"bound": "alu", "kernel": "wide_fwd_kernel", "achieved": achieved, "peak": peak,
                        "unit": "TFLOP/s", "frac": achieved / peak, "kernel_ms": fwd, "cells": cells}
+    # with 8 sequences the 64 MB logA cannot stay on chip (all shared memory
+    # together holds about 34 MB), so every step re-reads it: the step is
+    # bound by that stream, 4 K^2 bytes per step
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    lo_bytes = 4.0 * K * K * (T - 1)
+    hbm_ach = lo_bytes / (fwd / 1e3) / 1e9
+    out["roofline_hbm"] = {"bound": "hbm", "kernel": "wide_fwd_kernel", "achieved": hbm_ach, "peak": hbm_peak,
+                           "unit": "GB/s", "frac": hbm_ach / hbm_peak, "bytes_per_step": 4 * K * K,
+                           "alu_fraction_at_hbm_peak": (2.0 * n * K * K * hbm_peak * 1e9 / (4.0 * K * K)) / 1e12 / peak}
     del res, E
     torch.cuda.empty_cache()
     return out
