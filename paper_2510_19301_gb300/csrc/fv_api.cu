@@ -680,6 +680,10 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
         da.wide_X = reinterpret_cast<float*>(w);
         w += align_up(2 * sizeof(float) * lanes_k);
         da.wide_flags = reinterpret_cast<uint32_t*>(w);
+        w += align_up(sizeof(uint32_t) * 8 * (size_t)(device_sm_count() + 1));
+        float* at = reinterpret_cast<float*>(w);
+        da.wide_AT = at;
+        if (launch_wide_transpose(md.logA, md.K, at, st) != cudaSuccess) return FV_ECUDA;
       }
     }
     if (p->mode == FV_VANILLA) {

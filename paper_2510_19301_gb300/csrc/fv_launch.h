@@ -77,6 +77,7 @@ struct DenseArgs {
   uint16_t* wide_M;
   float* wide_X;
   uint32_t* wide_flags;
+  const float* wide_AT;       // column-major copy of logA: AT[j * lane_stride + i] = A[i][j]
   int32_t wide_withhold;      // test hook: CTA 0 never publishes its step count
   int32_t no_tune;            // use the default engine configuration, not the tuned one
   WsHeader* hdr;
@@ -158,6 +159,8 @@ int device_sm_count();
 bool wide_geometry(int K, int nsm, WideGeom* g);
 size_t wide_scratch_bytes(int K, int nsm);
 cudaError_t launch_wide_forward(DenseArgs a, cudaStream_t st);
+// AT[j * KD + i] = logA[i * K + j] (rows K..KD-1 are -inf), KD = wide_lane_stride(K).
+cudaError_t launch_wide_transpose(const float* logA, int K, float* AT, cudaStream_t st);
 void dense_stream_geometry(int K, int* KPM, int* cols);
 cudaError_t launch_ap_prep(const float* logA, int K, float2* Ap, cudaStream_t st);
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t st);

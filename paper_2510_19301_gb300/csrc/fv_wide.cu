@@ -100,11 +100,6 @@ __device__ __forceinline__ void cp_async16_keep(void* smem_dst, const void* gmem
   asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "l"(pol)
                : "memory");
 }
-__device__ __forceinline__ unsigned long long ldg64_keep(const unsigned long long* p, uint64_t pol) {
-  unsigned long long v;
-  asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
-  return v;
-}
 // Bytes of logA the whole grid streams per step, and the share of them to
 // keep in L2 (about 48 MB of a 126 MB L2 is left to the rest of the step).
 float wide_l2_keep(const WideGeom& g) {
@@ -193,10 +188,33 @@ bool wide_geometry(int K, int nsm, WideGeom* g) {
 }
 
 size_t wide_scratch_bytes(int K, int nsm) {
-  // delta and MidState double buffers, sub snapshots (job parity), flags
+  // delta and MidState double buffers, sub snapshots (job parity), flags,
+  // and the column-major copy of logA read by the owners' re-scan
   const size_t lk = (size_t)kWS * wide_lane_stride(K);
   return align_up(2 * sizeof(float) * lk) + align_up(2 * sizeof(uint16_t) * lk) + align_up(2 * sizeof(float) * lk) +
-         align_up(sizeof(uint32_t) * 8 * (size_t)(nsm + 1));
+         align_up(sizeof(uint32_t) * 8 * (size_t)(nsm + 1)) +
+         align_up(sizeof(float) * (size_t)K * wide_lane_stride(K));
+}
+
+// 32 x 32 tiles through shared memory, so both sides are coalesced.
+__global__ void wide_transpose_kernel(const float* logA, int K, int KD, float* AT) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < K && j < K) ? logA[(int64_t)i * K + j] : -CUDART_INF_F;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < K && i < KD) AT[(int64_t)j * KD + i] = tile[threadIdx.x][r];
+  }
+}
+
+cudaError_t launch_wide_transpose(const float* logA, int K, float* AT, cudaStream_t st) {
+  const int KD = wide_lane_stride(K);
+  wide_transpose_kernel<<<dim3((K + 31) / 32, (KD + 31) / 32), dim3(32, 8), 0, st>>>(logA, K, KD, AT);
+  return cudaGetLastError();
 }
 
 template <int CR>
@@ -617,14 +635,20 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
         }
         const int rowc = rb * RPC + (int)sRI[base + rb * kWS * JO] * kWCH;
         const float4* dsrc = reinterpret_cast<const float4*>(a.wide_D + cur * SK + (int64_t)os * KD + rowc);
-        const unsigned long long* asrc =
-            reinterpret_cast<const unsigned long long*>(a.Ap + (int64_t)(rowc / 2) * a.ap_stride + oj);
-        float4 dv[kWCH / 4];
-        unsigned long long avv[kWCH / 2];
+        // the chunk's 32 transition weights into column oj are contiguous in
+        // the column-major copy: eight 16-byte loads
+        const float4* asrc = reinterpret_cast<const float4*>(a.wide_AT + (int64_t)oj * KD + rowc);
+        float4 dv[kWCH / 4], av4[kWCH / 4];
 #pragma unroll
         for (int k2 = 0; k2 < kWCH / 4; ++k2) dv[k2] = dsrc[k2];
 #pragma unroll
-        for (int k2 = 0; k2 < kWCH / 2; ++k2) avv[k2] = ldg64_keep(asrc + (int64_t)k2 * a.ap_stride, pol);
+        for (int k2 = 0; k2 < kWCH / 4; ++k2) av4[k2] = __ldg(asrc + k2);
+        unsigned long long avv[kWCH / 2];
+#pragma unroll
+        for (int k2 = 0; k2 < kWCH / 4; ++k2) {
+          avv[2 * k2] = ((unsigned long long)__float_as_uint(av4[k2].y) << 32) | __float_as_uint(av4[k2].x);
+          avv[2 * k2 + 1] = ((unsigned long long)__float_as_uint(av4[k2].w) << 32) | __float_as_uint(av4[k2].z);
+        }
         uint4 mv[kWCH / 8];
 #pragma unroll
         for (int k2 = 0; k2 < kWCH / 8; ++k2) mv[k2] = make_uint4(0u, 0u, 0u, 0u);
