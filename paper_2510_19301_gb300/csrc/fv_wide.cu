@@ -284,6 +284,28 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
     if (bad) return;  // no peer touches this CTA's shared memory any more
   }
 
+  // this warp's streamed logA rows (the same every step) and its ring
+  float2* ring = sRing + warp * kWNST * 2 * kWJ;
+  const int NIT = (RPW - RWR) / 4;
+  const float2* gsrc = a.Ap + (int64_t)((row0 + warp * RPW + RWR) / 2) * a.ap_stride + j0;
+  auto issue = [&](int it) {
+    float2* dst = ring + (it % kWNST) * 2 * kWJ;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int qq = lane + 32 * u, pr = qq / (kWJ / 2), c2 = (qq % (kWJ / 2)) * 2;
+      cp_async16_keep(dst + pr * kWJ + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2, pol);
+    }
+  };
+  // the first kWNST-1 stages of a step, one commit group each
+  auto prefetch_ring = [&]() {
+#pragma unroll
+    for (int k2 = 0; k2 < kWNST - 1; ++k2) {
+      if (k2 < NIT) issue(k2);
+      cp_async_commit();
+    }
+  };
+  bool ring_ready = false;
+
   uint32_t tau = 0;
   for (;;) {
     const int cur = tau & 1, nxt = cur ^ 1;
@@ -529,22 +551,8 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
         const float2* aw = sA + (size_t)warp * (RWR / 2) * kWJ + 2 * jg;
 #pragma unroll 1
         for (int q = 0; q < RWR / 4; ++q) quad(lr0 + 4 * q, aw + (2 * q) * kWJ);
-        float2* ring = sRing + warp * kWNST * 2 * kWJ;
-        const int NIT = (RPW - RWR) / 4;
-        const float2* gsrc = a.Ap + (int64_t)((row0 + lr0 + RWR) / 2) * a.ap_stride + j0;
-        auto issue = [&](int it) {
-          float2* dst = ring + (it % kWNST) * 2 * kWJ;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int qq = lane + 32 * u, pr = qq / (kWJ / 2), c2 = (qq % (kWJ / 2)) * 2;
-            cp_async16_keep(dst + pr * kWJ + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2, pol);
-          }
-        };
-#pragma unroll
-        for (int k2 = 0; k2 < kWNST - 1; ++k2) {
-          if (k2 < NIT) issue(k2);
-          cp_async_commit();
-        }
+        if (!ring_ready) prefetch_ring();  // else issued during the previous step's tail
+        ring_ready = false;
 #pragma unroll 1
         for (int it = 0; it < NIT; ++it) {
           cp_async_wait<kWNST - 2>();
@@ -608,6 +616,10 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
 #pragma unroll
     for (int rr = 0; rr < CR; ++rr) abort_any |= s_abort[cur][rr];
     if (abort_any) break;
+    // the next step streams the same logA rows: start its first ring stages
+    // now, so they load during the owner phase and the waits below
+    prefetch_ring();
+    ring_ready = true;
 
     // ---- owners: lowest rank holding the maximum, + E_t, stores
 #pragma unroll
@@ -709,6 +721,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
     }
     ++tau;
   }
+  cp_async_wait<0>();   // no copy into this CTA's shared memory is left in flight
   cluster_sync_all();  // no CTA leaves while a peer may still write into its shared memory
 }
 
