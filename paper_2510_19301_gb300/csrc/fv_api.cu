@@ -100,7 +100,7 @@ struct FlashPlan {
   // budget leaves (exact FLASH with a backpointer budget): per model the
   // first level whose every task's rows fit the budget (-1: none), the
   // budget in rows, and an upper bound on the waves of that level
-  std::vector<int32_t> leaf_level, leaf_waves;
+  std::vector<int32_t> leaf_level, leaf_waves, leaf_cap;
   std::vector<int64_t> leaf_rows, leaf_tasks;
   int32_t waves_max = 0;
   size_t leaf_bytes = 0;
@@ -125,7 +125,7 @@ std::vector<int32_t> host_order(const fv_batch* b, bool nosort) {
 // then children in parent order), packed greedily into waves of at most R
 // backpointer rows.  Returns the wave count; *max_wave = the largest wave.
 int32_t host_leaf_waves(const fv_batch* b, const std::vector<int32_t>& order, int32_t model, int32_t P,
-                        int32_t level, int64_t R, int64_t* max_wave) {
+                        int32_t level, int64_t R, int32_t cap, int64_t* max_wave) {
   std::vector<int32_t> cur, nxt;
   for (int32_t i : order) {
     if ((b->model_host ? b->model_host[i] : 0) != model) continue;
@@ -151,7 +151,7 @@ int32_t host_leaf_waves(const fv_batch* b, const std::vector<int32_t>& order, in
   *max_wave = 0;
   for (size_t i = 0; i < cur.size(); ++i) {
     const int64_t r = cur[i] - 1;
-    if (used + r > R && (int64_t)i > first) {
+    if ((used + r > R || (cap > 0 && (int64_t)i - first >= cap)) && (int64_t)i > first) {
       *max_wave = std::max<int64_t>(*max_wave, (int64_t)i - first);
       ++waves;
       first = (int64_t)i;
@@ -173,6 +173,7 @@ FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b
   fp.max_tasks.assign(n_models, 0);
   fp.leaf_level.assign(n_models, -1);
   fp.leaf_waves.assign(n_models, 0);
+  fp.leaf_cap.assign(n_models, 0);
   fp.leaf_rows.assign(n_models, 0);
   fp.leaf_tasks.assign(n_models, 0);
   std::vector<std::vector<int64_t>> per(n_models), maxlen(n_models), rows(n_models);
@@ -217,7 +218,8 @@ FlashPlan plan_flash(const fv_model* models, int32_t n_models, const fv_batch* b
       fp.leaf_rows[m] = R;
       if (order.empty()) order = host_order(b, nosort);
       int64_t mw = 0;
-      fp.leaf_waves[m] = host_leaf_waves(b, order, m, P, (int32_t)l, R, &mw);
+      fp.leaf_cap[m] = dense_job_slots(models[m].K);
+      fp.leaf_waves[m] = host_leaf_waves(b, order, m, P, (int32_t)l, R, fp.leaf_cap[m], &mw);
       fp.leaf_tasks[m] = mw;
       fp.waves_max = std::max(fp.waves_max, fp.leaf_waves[m]);
       fp.leaf_bytes = std::max(fp.leaf_bytes, (size_t)R * (size_t)models[m].K * sizeof(uint16_t));
@@ -729,8 +731,8 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
         int32_t* wave_first = reinterpret_cast<int32_t*>(ws + L.waves);
         int32_t* wave_count = wave_first + fp.waves_max;
         uint16_t* leaf = reinterpret_cast<uint16_t*>(ws + L.leaf);
-        if (launch_leaf_plan(lists[c], &counts[c], fp.leaf_rows[m], wave_first, wave_count, fp.leaf_waves[m], hdr,
-                             st) != cudaSuccess)
+        if (launch_leaf_plan(lists[c], &counts[c], fp.leaf_rows[m], fp.leaf_cap[m], wave_first, wave_count,
+                             fp.leaf_waves[m], hdr, st) != cudaSuccess)
           return FV_ECUDA;
         for (int w = 0; w < fp.leaf_waves[m]; ++w) {
           if (launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;

@@ -928,6 +928,51 @@ int device_sm_count() {
   return nsm;
 }
 
+// Jobs the engine runs at once for K's class (default configuration):
+// resident clusters x slots; 0 when no device is visible.
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8>
+static int dense_cfg_slots() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW>;
+  int dev = 0, nsm = 0, resident = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return cached = 0;
+  }
+  if (CL > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL * nsm);
+    cfg.blockDim = dim3(Cfg::NT);
+    cfg.dynamicSmemBytes = Cfg::smem_bytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) != cudaSuccess) resident = 0;
+  } else {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::smem_bytes) != cudaSuccess) per_sm = 0;
+    resident = per_sm * nsm;
+  }
+  cudaGetLastError();
+  return cached = resident * S;
+}
+
+int dense_job_slots(int K) {
+  if (K > 1024) return kWideLanes;
+  if (K <= 64) return dense_cfg_slots<64, 16, 4, 1, 64, false>();
+  if (K <= 128) return dense_cfg_slots<128, 8, 16, 1, 128, false, 4>();
+  if (K <= 256) return dense_cfg_slots<128, 8, 16, 2, 256, false, 4>();
+  if (K <= 512) return dense_cfg_slots<128, 8, 8, 4, 512, true>();
+  return dense_cfg_slots<128, 8, 8, 8, 1024, true>();
+}
+
 int dense_supported_K(int K) {
   if (K >= 1 && K <= 1024) return 1;
   WideGeom g;

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kScanBlock) child_pass3(const Task* in, const 
 constexpr int kLeafChunk = 4096;
 
 __global__ void __launch_bounds__(1024) leaf_plan_kernel(Task* tasks, const int32_t* count, int64_t budget_rows,
-                                                         int32_t* wave_first, int32_t* wave_count,
+                                                         int32_t wave_cap, int32_t* wave_first, int32_t* wave_count,
                                                          int32_t max_waves, WsHeader* hdr) {
   __shared__ int32_t rows[kLeafChunk];
   __shared__ int32_t w_s, first_s;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(1024) leaf_plan_kernel(Task* tasks, const int3
       long long used = used_s;
       for (int i = 0; i < cn; ++i) {
         const int gi = base + i, r = rows[i];
-        if (used + r > budget_rows && gi > first) {
+        if ((used + r > budget_rows || (wave_cap > 0 && gi - first >= wave_cap)) && gi > first) {
           if (w < max_waves) {
             wave_first[w] = first;
             wave_count[w] = gi - first;
@@ -310,9 +310,10 @@ __global__ void __launch_bounds__(128) leaf_backtrack_kernel(const Task* tasks, 
   }
 }
 
-cudaError_t launch_leaf_plan(Task* tasks, const int32_t* count, int64_t budget_rows, int32_t* wave_first,
-                             int32_t* wave_count, int32_t max_waves, WsHeader* hdr, cudaStream_t st) {
-  leaf_plan_kernel<<<1, 1024, 0, st>>>(tasks, count, budget_rows, wave_first, wave_count, max_waves, hdr);
+cudaError_t launch_leaf_plan(Task* tasks, const int32_t* count, int64_t budget_rows, int32_t wave_cap,
+                             int32_t* wave_first, int32_t* wave_count, int32_t max_waves, WsHeader* hdr,
+                             cudaStream_t st) {
+  leaf_plan_kernel<<<1, 1024, 0, st>>>(tasks, count, budget_rows, wave_cap, wave_first, wave_count, max_waves, hdr);
   return cudaGetLastError();
 }
 

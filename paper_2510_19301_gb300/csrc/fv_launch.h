@@ -152,6 +152,7 @@ struct ScoreArgs {
 int dense_supported_K(int K);
 // Engine configuration variants of a K class and the tuned choice.
 int dense_k_class(int K);
+int dense_job_slots(int K);
 int dense_variants(int K);
 void dense_set_variant(int K, int v);
 int dense_get_variant(int K);
@@ -190,11 +191,14 @@ cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st);
 cudaError_t launch_check_inputs(const fv_model& m, int32_t model, const Job* jobs, int32_t n_seq, const float* E,
                                 const int32_t* obs, WsHeader* hdr, cudaStream_t st);
 // Budget leaves: greedy packing of a task list into waves whose backpointer
-// rows (n - m per task) fit budget_rows; writes each task's row offset into
+// rows (n - m per task) fit budget_rows and that hold at most wave_cap tasks
+// (0: no cap; the engine's concurrent job slots, so a wave runs in one
+// round); writes each task's row offset into
 // Task::pad and the waves' [first, count) into wave_first / wave_count
 // (max_waves entries, unused ones empty).
-cudaError_t launch_leaf_plan(Task* tasks, const int32_t* count, int64_t budget_rows, int32_t* wave_first,
-                             int32_t* wave_count, int32_t max_waves, WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_leaf_plan(Task* tasks, const int32_t* count, int64_t budget_rows, int32_t wave_cap,
+                             int32_t* wave_first, int32_t* wave_count, int32_t max_waves, WsHeader* hdr,
+                             cudaStream_t st);
 // q_{t-1} = psi_t[q_t] from the known q_n down to t = m + 1 for every task of
 // one wave (max_count bounds the wave's size).
 cudaError_t launch_leaf_backtrack(const Task* tasks, const int32_t* wave_first, const int32_t* wave_count,
