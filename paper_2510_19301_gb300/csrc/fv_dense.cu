@@ -157,10 +157,6 @@ struct Slot {
   int32_t state, term, t;
   int32_t kdiv, ediv, eprev;  // root: next division point index / value, previous one (-1: none)
   int32_t tmid;               // sub: midpoint of the segment
-  int32_t f_mid;              // this tick: 0 no MidState, 1 MidState = psi, 2 MidState = MidState_prev[psi]
-  int32_t f_snap, f_map, f_k; // this tick: snapshot delta / store ancestor map / division index
-  int32_t sym;                // this tick: observation symbol (discrete emissions)
-  const float* erow;          // this tick: emission row E_t (dense emissions)
   PJob cur, pend;
 };
 
