@@ -236,6 +236,7 @@ struct Layout {
   size_t bscratch, div_id, div_val, div_mid, div_n;
   size_t ap, snapx;  // streamed exact configurations (K > 256)
   size_t wide;       // whole-GPU configuration scratch (K > 1024)
+  size_t at;         // column-major logA copy of the streamed configurations (256 < K <= 1024)
   uint64_t aux_elems;
   int64_t map_stride, snap_stride, list_cap;
   int32_t Wcap, Bcap, pe_cap, max_ctas;
@@ -321,6 +322,14 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
       if (kmax > 1024) {
         L.wide = end;
         end = align_up(L.wide + wide_scratch_bytes(kmax, nsm));
+      }
+      // streamed models (K <= 1024) share one column-major copy, sized for the largest
+      int32_t ks = 0;
+      for (int m = 0; m < n_models; ++m)
+        if (models[m].K > 256 && models[m].K <= 1024) ks = std::max(ks, models[m].K);
+      if (ks) {
+        L.at = end;
+        end = align_up(L.at + sizeof(float) * (size_t)ks * wide_lane_stride(ks));
       }
     }
   }
@@ -670,6 +679,11 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
         da.ap_stride = cols;
         da.snap_scratch = reinterpret_cast<float*>(ws + L.snapx);
         if (launch_ap_prep(md.logA, md.K, reinterpret_cast<float2*>(ws + L.ap), st) != cudaSuccess) return FV_ECUDA;
+        if (md.K <= 1024) {
+          float* at = reinterpret_cast<float*>(ws + L.at);
+          da.wide_AT = at;
+          if (launch_wide_transpose(md.logA, md.K, at, st) != cudaSuccess) return FV_ECUDA;
+        }
       }
       if (md.K > 1024) {
         // whole-GPU engine scratch: the same carving as wide_scratch_bytes

@@ -220,13 +220,13 @@ struct DenseCfg {
   static constexpr int NST = KPM <= 512 ? 8 : 5;  // streamed: ring stages of 4 rows per warp
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
   static_assert(LJ * LS == 32 && LS * 4 == S && (TW == 8 || TW == 4), "lane tile is 4 sequences x TW columns");
-  static_assert(J % WC == 0 && NW % CG == 0 && (!STREAM || (TW == 8 && CG == 1)), "warp tiling");
+  static_assert(J % WC == 0 && NW % CG == 0 && WC % 32 == 0, "warp tiling");
   static_assert((S * J) % NT == 0 && NT % J == 0, "epilogue: one column per thread, OPT slots");
   static_assert(C % CH == 0 && CH % 4 == 0 && (32 % CH == 0 || CH % 32 == 0), "chunks inside skew blocks");
   static_assert(!STREAM || C / CH <= 255 * 1, "chunk ids fit a byte");
   // resident: logA slab [KP/2][J] float2; streamed: per-warp ring of NST
   // stages x 2 row pairs x J float2, plus the chunk id of each partial
-  static constexpr size_t a_floats = STREAM ? (size_t)NW * NST * 4 * J : (size_t)KP * J;
+  static constexpr size_t a_floats = STREAM ? (size_t)NW * NST * 4 * WC : (size_t)KP * J;
   static constexpr size_t snap_floats = STREAM ? 0 : (size_t)S * KP;
   static constexpr size_t smem_bytes =
       sizeof(float) * (a_floats + 2ull * S * KPS + (size_t)RG * S * J + snap_floats) +
@@ -456,30 +456,32 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
     // columns] as row pairs and issues one add.f32x2 + one 3-input max per
     // 2 cells.
     if constexpr (STREAM) {
-      // streamed: this warp's C rows of logA arrive 4 rows at a time through
-      // an NST-stage cp.async ring; chunk winners (first chunk of CH rows
-      // reaching the running maximum) are kept per output in registers
+      // streamed: this warp's C rows (its row group) of its WC columns
+      // arrive 4 rows at a time through an NST-stage cp.async ring; chunk
+      // winners (first chunk of CH rows reaching the running maximum) are
+      // kept per output in registers
       const int sg = lane / LJ, jg = lane % LJ;
-      float acc[4][8], bst[4][8];
-      int bch[4][8];
+      const int cg = warp % CG, rg = warp / CG;
+      float acc[4][TW], bst[4][TW];
+      int bch[4][TW];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) {
+        for (int y = 0; y < TW; ++y) {
           acc[x][y] = -CUDART_INF_F;
           bst[x][y] = -CUDART_INF_F;
           bch[x][y] = 0;
         }
-      const int i0 = warp * C;
-      float2* ring = reinterpret_cast<float2*>(sA) + warp * NST * 2 * J;
-      const float2* gsrc = a.Ap + (int64_t)(i0 / 2) * a.ap_stride + j0;
+      const int i0 = rg * C;
+      float2* ring = reinterpret_cast<float2*>(sA) + warp * NST * 2 * WC;
+      const float2* gsrc = a.Ap + (int64_t)(i0 / 2) * a.ap_stride + j0 + cg * WC;
       constexpr int NIT = C / 4;
       auto issue = [&](int it) {
-        float2* dst = ring + (it % NST) * 2 * J;
+        float2* dst = ring + (it % NST) * 2 * WC;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int q = lane + 32 * u, pr = q / (J / 2), c2 = (q % (J / 2)) * 2;
-          cp_async16(dst + pr * J + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
+        for (int u = 0; u < WC / 32; ++u) {
+          const int q = lane + 32 * u, pr = q / (WC / 2), c2 = (q % (WC / 2)) * 2;
+          cp_async16(dst + pr * WC + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
         }
       };
 #pragma unroll
@@ -496,31 +498,31 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         cp_async_commit();
         const int i = i0 + 4 * it;
         const float* dbase = dbase0 + i + ((i >> 5) << 2);
-        const float2* abase = ring + (it % NST) * 2 * J + 2 * jg;
+        const float2* abase = ring + (it % NST) * 2 * WC + 2 * jg;
         ulonglong2 dq[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) dq[x] = *reinterpret_cast<const ulonglong2*>(dbase + x * KPS);
-        ulonglong2 aq[2][4];
+        ulonglong2 aq[2][TW / 2];
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-          for (int g = 0; g < 4; ++g)
-            aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + pr * J + 2 * LJ * g);
+          for (int g = 0; g < TW / 2; ++g)
+            aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + pr * WC + 2 * LJ * g);
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
+          for (int g = 0; g < TW / 2; ++g) {
             fadd2_max3(acc[x][2 * g], dq[x].x, aq[0][g].x);
             fadd2_max3(acc[x][2 * g], dq[x].y, aq[1][g].x);
             fadd2_max3(acc[x][2 * g + 1], dq[x].x, aq[0][g].y);
             fadd2_max3(acc[x][2 * g + 1], dq[x].y, aq[1][g].y);
           }
         if ((it + 1) % (CH / 4) == 0) {
-          const int c = warp * (C / CH) + it / (CH / 4);
+          const int c = rg * (C / CH) + it / (CH / 4);
 #pragma unroll
           for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 8; ++y) {
+            for (int y = 0; y < TW; ++y) {
               if (acc[x][y] > bst[x][y]) { bst[x][y] = acc[x][y]; bch[x][y] = c; }
               acc[x][y] = -CUDART_INF_F;
             }
@@ -529,10 +531,10 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       cp_async_wait<0>();
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        float* pp = sPart + (warp * S + sg * 4 + x) * J + 2 * jg;
-        uint8_t* pc = sPC + (warp * S + sg * 4 + x) * J + 2 * jg;
+        float* pp = sPart + (rg * S + sg * 4 + x) * J + cg * WC + 2 * jg;
+        uint8_t* pc = sPC + (rg * S + sg * 4 + x) * J + cg * WC + 2 * jg;
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 0; g < TW / 2; ++g) {
           *reinterpret_cast<float2*>(pp + 2 * LJ * g) = make_float2(bst[x][2 * g], bst[x][2 * g + 1]);
           pc[2 * LJ * g] = (uint8_t)bch[x][2 * g];
           pc[2 * LJ * g + 1] = (uint8_t)bch[x][2 * g + 1];
@@ -623,19 +625,33 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         ar[r] = STREAM ? a.Ap + (int64_t)(wbase[r] / 2) * a.ap_stride + jcol : sA2 + (wbase[r] / 2) * J + jj;
       }
       if constexpr (STREAM) {
-        // streamed: the chunk's logA pairs come from L2; load one output's
-        // CH/2 pairs at once so their latencies overlap, then compare
+        // streamed: the chunk's CH weights into column jcol are contiguous
+        // in the column-major copy (L2); two outputs' loads are in flight at
+        // once, then compared row by row
+        const int KD = wide_lane_stride(K);
 #pragma unroll
-        for (int r = 0; r < OPT; ++r) {
-          unsigned long long av[CH / 2];
+        for (int r0 = 0; r0 < OPT; r0 += 2) {
+          float4 a4[2][CH / 4];
 #pragma unroll
-          for (int k = 0; k < CH / 2; ++k) av[k] = __ldg(reinterpret_cast<const unsigned long long*>(ar[r] + k * astr));
+          for (int u = 0; u < 2; ++u) {
+            const float4* src = reinterpret_cast<const float4*>(a.wide_AT + (int64_t)jcol * KD + wbase[r0 + u]);
 #pragma unroll
-          for (int k = CH / 2 - 1; k >= 0; --k) {
-            float c0, c1;
-            fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k), av[k], c0, c1);
-            if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
-            if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+            for (int k = 0; k < CH / 4; ++k) a4[u][k] = __ldg(src + k);
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int r = r0 + u;
+#pragma unroll
+            for (int k = CH / 2 - 1; k >= 0; --k) {
+              const float4 q = a4[u][k / 2];
+              const float lo = (k & 1) ? q.z : q.x, hi = (k & 1) ? q.w : q.y;
+              const unsigned long long av =
+                  ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
+              float c0, c1;
+              fadd2(*reinterpret_cast<const unsigned long long*>(dr[r] + 2 * k), av, c0, c1);
+              if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
+              if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+            }
           }
         }
       } else {
@@ -1028,6 +1044,8 @@ int dense_variants(int K) {
     case 0: return 3;
     case 1: return 2;
     case 2: return 2;
+    case 3: return 2;
+    case 4: return 2;
     default: return 1;
   }
 }
@@ -1056,7 +1074,11 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     if (v == 1) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
     return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);
   }
-  if (a.K <= 512) return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
+  if (a.K <= 512) {
+    if (v == 1) return launch_dense_cfg<128, 8, 16, 4, 512, true, 4>(a, max_clusters, st);
+    return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
+  }
+  if (v == 1) return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4>(a, max_clusters, st);
   return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);
 }
 

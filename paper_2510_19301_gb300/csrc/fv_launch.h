@@ -77,7 +77,8 @@ struct DenseArgs {
   uint16_t* wide_M;
   float* wide_X;
   uint32_t* wide_flags;
-  const float* wide_AT;       // column-major copy of logA: AT[j * lane_stride + i] = A[i][j]
+  const float* wide_AT;       // column-major copy of logA, AT[j * wide_lane_stride(K) + i] = A[i][j]
+                              // (streamed and whole-GPU configurations: the exact re-scan reads it)
   int32_t wide_withhold;      // test hook: CTA 0 never publishes its step count
   int32_t no_tune;            // use the default engine configuration, not the tuned one
   WsHeader* hdr;

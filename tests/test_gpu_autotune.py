@@ -23,7 +23,7 @@ def bits(a):
     return np.asarray(a, np.float32).view(np.int32)
 
 
-@pytest.mark.parametrize("K", [37, 64, 100, 128, 200, 256])
+@pytest.mark.parametrize("K", [37, 64, 100, 128, 200, 256, 300, 512, 777, 1024])
 def test_every_variant_matches_oracle(fv, K):
     rng = np.random.default_rng(K + 900)
     log_pi, logA = W.random_model(K, rng)
