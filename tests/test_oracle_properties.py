@@ -1,0 +1,78 @@
+"""Property-based checks of the oracle (hypothesis, CPU): for random small
+models the exact decoder reaches the brute-force optimum, and every
+exact variant of the paper's method (FLASH for any P, with or without a
+backpointer budget; the beam with every state kept) returns the same path
+and score bit for bit; the returned score is the path's own
+forward-order log-likelihood."""
+import itertools
+
+import numpy as np
+import pytest
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+import oracle  # noqa: E402
+
+
+def model_strategy(max_k=4, max_t=6, integer=False):
+    @st.composite
+    def draw(d):
+        K = d(st.integers(1, max_k))
+        T = d(st.integers(1, max_t))
+        seed = d(st.integers(0, 2 ** 31 - 1))
+        rng = np.random.default_rng(seed)
+        if integer:
+            lp = rng.integers(-2, 3, K).astype(np.float32)
+            A = rng.integers(-2, 3, (K, K)).astype(np.float32)
+            E = rng.integers(-2, 3, (T, K)).astype(np.float32)
+        else:
+            lp = rng.standard_normal(K).astype(np.float32)
+            A = rng.standard_normal((K, K)).astype(np.float32)
+            E = rng.standard_normal((T, K)).astype(np.float32)
+        if d(st.booleans()):
+            A[rng.random((K, K)) < 0.3] = -np.inf
+        return lp, A, E
+    return draw()
+
+
+def brute_best(lp, A, E):
+    T, K = E.shape
+    best = -np.inf
+    for q in itertools.product(range(K), repeat=T):
+        s = np.float32(lp[q[0]] + E[0, q[0]])
+        for t in range(1, T):
+            s = np.float32(np.float32(s + A[q[t - 1], q[t]]) + E[t, q[t]])
+        best = max(best, float(s))
+    return best
+
+
+def bits(x):
+    return np.float32(x).view(np.int32)
+
+
+@settings(max_examples=150, deadline=None)
+@given(model_strategy(), st.integers(1, 8), st.integers(0, 6))
+def test_exact_variants_agree(case, P, budget):
+    lp, A, E = case
+    hmm = oracle.HMM(lp, A)
+    pv, sv = oracle.viterbi(hmm, E)
+    assert float(sv) == brute_best(lp, A, E)
+    pf, sf, _ = oracle.flash(hmm, E, P)
+    pb, sb, _, _ = oracle.flash_budget(hmm, E, P, budget)
+    assert np.array_equal(pv, pf) and bits(sv) == bits(sf)
+    assert np.array_equal(pv, pb) and bits(sv) == bits(sb)
+    if np.isfinite(sv):
+        assert bits(oracle.path_score(hmm, E, pv)) == bits(sv)
+        pw, sw, rc = oracle.beam(hmm, E, lp.shape[0])
+        assert rc == 0 and np.array_equal(pv, pw) and bits(sv) == bits(sw)
+
+
+@settings(max_examples=100, deadline=None)
+@given(model_strategy(max_k=5, max_t=9, integer=True), st.integers(1, 9))
+def test_integer_ties_flash_equals_vanilla(case, P):
+    lp, A, E = case
+    hmm = oracle.HMM(lp, A)
+    pv, sv = oracle.viterbi(hmm, E)
+    pf, sf, _ = oracle.flash(hmm, E, P)
+    assert np.array_equal(pv, pf) and bits(sv) == bits(sf)
