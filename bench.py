@@ -36,7 +36,7 @@ WORKLOAD = "batched-uneven: 1024 seqs, K=256 dense FP32, T~U[500,4000], E=log_so
 # DRAM bytes per state-step of dense_fwd_kernel (K=256, vanilla): reads of
 # E plus writes of psi, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 128-sequence launch of this workload.
-DRAM_BYTES_PER_STATE_STEP = (279012864 + 110379776) / (271316 * 256)
+DRAM_BYTES_PER_STATE_STEP = (280835072 + 109482240) / (271316 * 256)
 
 
 def dist_env():
@@ -207,6 +207,133 @@ def per_sequence_comparator(fv, m, lengths, E, K, n_sample, device):
     steps = int(lengths[:n_sample].astype(np.int64).sum()) * K
     return {"value": steps / (ms / 1e3), "unit": UNIT, "sample": f"first {n_sample} sequences, one launch each",
             "ms": ms}
+
+
+def config1_latency(fv, device, iters=200):
+    """One K=64 sequence of T=1000 discrete symbols (the small, latency-bound
+    workload): device time per decode, as back-to-back fv_decode calls and
+    as a CUDA graph replay of one decode."""
+    import torch
+
+    import workloads as W
+    w = W.config1()
+    m = fv.Model(w["log_pi"], w["logA"], logB=w["logB"], device=device)
+    b = fv.Batch([w["T"]], obs=w["obs"], models=[m], device=device)
+    steps = w["T"] * w["K"]
+    st = torch.cuda.Stream(device=device)
+    out = {"workload": "1 sequence, K=64, V=32 symbols, T=1000 (discrete emissions)"}
+    ref = None
+    for name, kw in (("vanilla", {"mode": "vanilla"}), ("flash_P16", {"mode": "flash", "P": 16}),
+                     ("beam_B16", {"mode": "beam", "B": 16, "P": 0})):
+        d = fv.Decoder([m], b, **kw)
+        with torch.cuda.stream(st):
+            d(st, check=True)
+            for _ in range(5):
+                d.launch(st)
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(iters):
+            d.launch(st)
+        e1.record(st)
+        st.synchronize()
+        us_launch = e0.elapsed_time(e1) * 1e3 / iters
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            d.launch(st)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        e0.record(st)
+        with torch.cuda.stream(st):
+            for _ in range(iters):
+                g.replay()
+        e1.record(st)
+        st.synchronize()
+        us_graph = e0.elapsed_time(e1) * 1e3 / iters
+        assert d.device_status(st) == 0
+        row = {"us_per_decode": us_launch, "us_per_decode_graph": us_graph,
+               "value": steps / (us_graph / 1e6), "unit": UNIT}
+        if name == "vanilla":
+            ref = (d.paths.clone(), d.scores.clone())
+        elif name == "flash_P16":
+            row["bit_identical_to_vanilla"] = bool(torch.equal(ref[0], d.paths) and torch.equal(
+                ref[1].view(torch.int32), d.scores.view(torch.int32)))
+        out[name] = row
+        del g, d
+    return out
+
+
+def config4_train(fv, device, steps=10, warmup=3):
+    """One training step of the CRF-style tagger (K=128 tags, 512 sequences
+    of 20..512 steps, 256 features): E = X W^T + b (a plain FP32 library
+    GEMM, TF32 off), scores = ViterbiScore (FLASH P=16 decode), loss = sum
+    of scores, backward (path counts through the emission layer)."""
+    import torch
+
+    import workloads as W
+    w = W.config4()
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        X = torch.from_numpy(w["X"]).to(device)
+        Wt = torch.from_numpy(w["W"]).to(device).requires_grad_(True)
+        bias = torch.from_numpy(w["b"]).to(device).requires_grad_(True)
+        log_pi = torch.from_numpy(w["log_pi"]).to(device).requires_grad_(True)
+        logA = torch.from_numpy(w["logA"]).to(device).requires_grad_(True)
+        lengths = w["T"]
+
+        def step():
+            for p in (Wt, bias, log_pi, logA):
+                p.grad = None
+            E = X @ Wt.t() + bias
+            scores = fv.ViterbiScore.apply(log_pi, logA, E, lengths, "flash", 16)
+            loss = scores.sum()
+            loss.backward()
+            return loss
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            loss = step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        state_steps = int(lengths.astype(np.int64).sum()) * w["K"]
+        # the decode alone (FLASH P=16) on the same emission scores
+        with torch.no_grad():
+            E = X @ Wt.t() + bias
+        m = fv.Model(log_pi.detach(), logA.detach(), device=device)
+        bt = fv.Batch(lengths, E=E.reshape(-1), models=[m], device=device)
+        d = fv.Decoder([m], bt, mode="flash", P=16)
+        d(check=True)
+        lib = fv._lib.load()
+        dms, _ = time_decoder(d, steps, 2, lib)
+        dpi, dA, _ = fv.backward(m, bt, d.paths, torch.ones(bt.n, device=device))
+        for _ in range(2):
+            fv.backward(m, bt, d.paths, torch.ones(bt.n, device=device))
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            fv.backward(m, bt, d.paths, torch.ones(bt.n, device=device))
+        e1.record(st)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / steps
+        # exactness of the count gradient: sum dlogA = sum_b (T_b - 1), sum dlog_pi = n (g = 1)
+        sums_exact = bool(float(dA.double().sum()) == float((lengths.astype(np.int64) - 1).sum())
+                          and float(dpi.double().sum()) == float(len(lengths)))
+        return {"workload": "512 sequences, T in [20, 512], K=128 tags, 256 features; E = X W^T + b",
+                "ms_per_train_step": ms, "value": state_steps / (ms / 1e3), "unit": UNIT,
+                "decode_flash_P16_ms": dms, "backward_ms": bms, "loss": float(loss.item()),
+                "count_gradient_sums_exact": sums_exact,
+                "note": "train step = emission GEMM + FLASH decode + path-count backward + GEMM gradients, "
+                        "through torch.autograd (host work included)"}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev_tf32
 
 
 def config3_dense(fv, T, device, lib):
@@ -502,6 +629,9 @@ def run_ours(args):
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
     if modes:
         out["modes"] = modes
+    if rank == 0 and not args.quick:
+        out["config1"] = config1_latency(fv, device)
+        out["config4_train"] = config4_train(fv, device)
     if rank == 0 and args.c3_T > 0:
         out["config3_dense"] = config3_dense(fv, args.c3_T, device, lib)
     if rank == 0 and args.c3s_T > 0:

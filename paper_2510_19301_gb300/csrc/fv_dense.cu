@@ -141,23 +141,37 @@ __global__ void __launch_bounds__(256) order_kernel(const Job* jobs, int32_t n, 
 }
 
 // ------------------------------------------------------------ forward engine
-enum SlotState : int32_t { kNeedPop = 0, kWaiting = 1, kRun = 2, kDone = 3 };
+enum SlotState : int32_t { kIdle = 0, kRun = 2, kDone = 3 };
 
-// A job as seen by a slot; rank 0 of the cluster fills it and copies it
-// word by word into every CTA, so all CTAs run identical slot states.
-struct PJob {
+// A job as seen by a slot; rank 0 of the cluster fills it and sends it to
+// every CTA, so all CTAs run identical slot states.
+struct __align__(16) PJob {
   int32_t valid, b, m, n, T, Pe, q_prev, q_n;
   float s_prev;
   int32_t pad;
   int64_t e_off, path_off, aux_off;
 };
-static_assert(sizeof(PJob) % 4 == 0, "PJob is copied as 32-bit words");
+static_assert(sizeof(PJob) % 16 == 0, "PJob is sent as 16-byte pieces");
 
-struct Slot {
-  int32_t state, term, t;
-  int32_t kdiv, ediv, eprev;  // root: next division point index / value, previous one (-1: none)
-  int32_t tmid;               // sub: midpoint of the segment
-  PJob cur, pend;
+// Slot state machine, replicated in every CTA of a cluster and run by the
+// thread whose index is the slot on a register copy.  The next job of a slot
+// is drawn one tick before its current job ends (or when the slot is idle);
+// in multi-CTA clusters a draw becomes usable two ticks later, once every CTA
+// has waited for the tick in which rank 0 sent it.
+struct __align__(16) Slot {
+  int32_t state, term, t, kdiv;  // kdiv, ediv, eprev: root division points (next index / value, previous)
+  int32_t ediv, eprev, tmid;     // tmid: sub midpoint of the segment
+  int32_t drawn;                 // a job was drawn for the slot and not yet taken
+  int32_t draw_tick;             // engine tick of that draw
+  int32_t ndraw;                 // draws so far; draw k is kept in pend[k & 1]
+  int32_t drawn_now;             // drawn in this tick's prologue
+  int32_t ev;                    // first job step (t) at which the prologue must run in full
+  PJob cur;
+};
+// What the termination of a job that ended in this tick's prologue reads.
+struct __align__(16) SlotFin {
+  int32_t b, m, n, q_n;
+  int64_t path_off, aux_off;
 };
 
 // What every thread needs to know about a slot during one tick, written by
@@ -165,7 +179,7 @@ struct Slot {
 struct __align__(16) TickDesc {
   int32_t mode;       // 0 idle, 1 first step of the job (init), 2 max-plus step
   int32_t f_mid;      // 0 none, 1 MidState = psi, 2 MidState = MidState_prev[psi]
-  int32_t f_snap;     // 1: root snapshot to global / sub snapshot to shared
+  int32_t f_snap;     // root: this tick's delta to the global snapshot; sub: rank 0 keeps delta_{t-1}
   int32_t q_prev;     // pruned start: q*_{m-1} (0 when m == 0)
   float s_prev;       // pruned start: retained offset
   int32_t first;      // 1 when t == 0 (start from pi)
@@ -174,8 +188,8 @@ struct __align__(16) TickDesc {
   int64_t snap_row;   // root: element offset of the snapshot row (f_snap)
   int64_t map_row;    // root: element offset of the map row, -1 if none
   int32_t sym;        // discrete emissions: observation symbol x_t
-  int32_t pad[3];
 };
+static_assert(sizeof(TickDesc) == 64, "tick descriptor: 64 bytes");
 
 // c = (d.lo + a.lo, d.hi + a.hi), two FP32 adds rounded to nearest even,
 // then acc = max(acc, c.lo, c.hi) with the 3-input max.
@@ -200,6 +214,10 @@ __host__ __device__ inline int32_t flash_pe(int32_t T, int32_t P) {
 __host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
   return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
 }
+
+// bounded wait of the multi-CTA exchange (~1 s at 2 GHz); on expiry the
+// engine records FV_ETIMEOUT and stops at the next tick
+constexpr long long kClusterWaitCycles = 1ll << 31;
 
 // TW = columns per lane (8, or 4 for the 16-warp configurations): a lane
 // holds 4 slots x TW columns; a warp covers all S slots and LJ*TW columns;
@@ -241,7 +259,18 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   constexpr int CH = Cfg::CH, NST = Cfg::NST;
   extern __shared__ __align__(16) float smem[];
   __shared__ Slot slots[S];
+  __shared__ PJob s_pend[S][2];
+  __shared__ SlotFin s_fin[S];
   __shared__ TickDesc tdesc[S];
+  static_assert(Cfg::smem_bytes + (sizeof(Slot) + 2 * sizeof(PJob) + sizeof(SlotFin) + sizeof(TickDesc)) * S + 64 <=
+                    227 * 1024,
+                "dynamic + static shared memory within the 227 KB a CTA may use");
+  // multi-CTA clusters: barrier b completes when delta_t (t & 1 == b) of
+  // every CTA is in this CTA's shared memory (local warps arrive, the other
+  // CTAs' 16-byte stores complete transaction bytes)
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_info[2][5];  // per tick parity: active / MidState / sub-snapshot / drawn / ended slot masks
+  __shared__ int s_abort;
 
   const int K = a.K;
   // resident: logA column slab as row pairs sA2[i/2][jj] = (A[i][j0+jj],
@@ -264,6 +293,13 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   // epilogue mapping: this thread owns column jj for slots s0 + r * (NT / J)
   const int jj = tid % J, jcol = j0 + jj, s0 = tid / J;
   constexpr int SSTEP = NT / J;
+  // delta exchange of multi-CTA clusters (measured per cluster size): two
+  // CTAs use plain remote stores and a cluster barrier per tick (0); larger
+  // clusters use 16-byte st.async stores that complete transaction bytes on
+  // the receiver's mbarrier, so no CTA waits for its stores to be
+  // acknowledged (1)
+  constexpr int kExch = CL <= 2 ? 0 : 1;
+  constexpr int kLag = CL == 1 ? 0 : (kExch == 0 ? 1 : 2);  // ticks from a draw until every CTA holds it
 
   if (a.hdr->status != 0) return;  // an earlier kernel recorded an error: do nothing
 
@@ -275,166 +311,252 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   }
   for (int x = tid; x < 2 * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
   for (int x = tid; x < 2 * S * KP; x += NT) sMid[x] = 0;
+
+  // next job for the slot: rank 0 draws an index from the shared counter and
+  // reads the job (other CTAs receive it)
+  auto fetch_job = [&]() -> PJob {
+    PJob pj;
+    pj.valid = 0;
+    pj.b = pj.m = pj.n = pj.T = pj.Pe = pj.q_prev = pj.q_n = pj.pad = 0;
+    pj.s_prev = 0.f;
+    pj.e_off = pj.path_off = pj.aux_off = 0;
+    const unsigned long long k = atomicAdd(a.pop, 1ull);
+    const bool from_tasks = kind == kJobSub || kind == kJobLeaf;
+    if (!from_tasks) {
+      if (k < (unsigned long long)a.order_count) {
+        const int b = a.order[a.order_begin + (int)k];
+        const Job jb = a.jobs[b];
+        pj.valid = 1;
+        pj.b = b;
+        pj.m = 0;
+        pj.n = jb.T - 1;
+        pj.T = jb.T;
+        pj.Pe = flash_pe(jb.T, a.P);
+        pj.e_off = jb.e_off;
+        pj.path_off = jb.path_off;
+        pj.aux_off = jb.aux_off;
+      }
+    } else if (k < (unsigned long long)*a.task_count) {
+      const Task tk = a.tasks[(a.task_first ? *a.task_first : 0) + (int64_t)k];
+      const Job jb = a.jobs[tk.b];
+      pj.valid = 1;
+      pj.b = tk.b;
+      pj.m = tk.m;
+      pj.n = tk.n;
+      pj.T = jb.T;
+      pj.e_off = jb.e_off;
+      pj.path_off = jb.path_off;
+      pj.aux_off = jb.aux_off;
+      pj.pad = tk.pad;
+      // states revealed by earlier levels; clamped so that no value can
+      // index shared memory outside the slab
+      const int qn = a.paths[jb.path_off + tk.n];
+      pj.q_n = (unsigned)qn < (unsigned)a.K ? qn : 0;
+      if (tk.m > 0) {
+        const int qp = a.paths[jb.path_off + tk.m - 1];
+        pj.q_prev = (unsigned)qp < (unsigned)a.K ? qp : 0;
+        pj.s_prev = a.sval[jb.aux_off + tk.m - 1];
+      }
+    }
+    return pj;
+  };
+  auto draw = [&](Slot& sl, int tick) {
+    const int k = sl.ndraw & 1;
+    sl.ndraw += 1;
+    sl.drawn = 1;
+    sl.draw_tick = tick;
+    sl.drawn_now = 1;
+    if (rank == 0) {
+      s_pend[tid][k] = fetch_job();
+      if constexpr (CL > 1 && kExch == 0) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&s_pend[tid][k]);
+        for (int w = 0; w < (int)(sizeof(PJob) / 4); ++w)
+          for (int r = 1; r < CL; ++r) dsmem_st_u32(dsmem_addr(src + w, r), src[w]);
+      }
+    }
+  };
+
+  // every slot starts with one job drawn before the first tick
   if (tid < S) {
-    slots[tid].state = kNeedPop;
-    slots[tid].term = 0;
-    slots[tid].pend.valid = 0;
+    Slot sl;
+    sl.state = kIdle;
+    sl.term = sl.t = sl.kdiv = sl.ediv = sl.eprev = sl.tmid = 0;
+    sl.drawn = 1;
+    sl.draw_tick = -kLag;
+    sl.ndraw = 1;
+    sl.drawn_now = 0;
+    sl.ev = 0;
+    sl.cur = PJob{};
+    slots[tid] = sl;
+    if (rank == 0) s_pend[tid][0] = fetch_job();
   }
+  if (tid == 0) s_abort = 0;
   // distributed shared memory bases of the peers (byte addresses)
-  uint32_t pD[CL], pMid[CL], pSnap[CL];
+  uint32_t pD[CL], pMid[CL], pBar0[CL], pBar1[CL];
 #pragma unroll
   for (int rr = 0; rr < CL; ++rr) {
     pD[rr] = CL > 1 ? dsmem_addr(sD, rr) : 0u;
     pMid[rr] = CL > 1 ? dsmem_addr(sMid, rr) : 0u;
-    pSnap[rr] = (CL > 1 && !STREAM) ? dsmem_addr(sSnap, rr) : 0u;
+    pBar0[rr] = CL > 1 ? dsmem_addr(&s_bar[0], rr) : 0u;
+    pBar1[rr] = CL > 1 ? dsmem_addr(&s_bar[1], rr) : 0u;
   }
-  if (CL > 1) cluster_sync_all(); else __syncthreads();
+  if constexpr (CL > 1) {
+    if (tid == 0) {
+      mbar_init(smem_addr(&s_bar[0]), NW);
+      mbar_init(smem_addr(&s_bar[1]), NW);
+      fence_mbar_init_cluster();
+    }
+    cluster_sync_all();  // every CTA of the cluster runs: its shared memory may be written
+    if (rank == 0 && tid < S) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&s_pend[tid][0]);
+      for (int w = 0; w < (int)(sizeof(PJob) / 4); ++w)
+        for (int r = 1; r < CL; ++r) dsmem_st_u32(dsmem_addr(src + w, r), src[w]);
+    }
+    cluster_sync_all();
+  } else {
+    __syncthreads();
+  }
 
   int cur = 0;
-  for (;;) {
+  int tick = 0;
+  for (;; ++tick) {
     // ---- prologue: slot state machine (identical in every CTA)
-    if (tid < S) {
-      Slot& sl = slots[tid];
-      sl.term = 0;
-      if (sl.state == kRun && sl.t > sl.cur.n) {
-        sl.term = 1;  // sl.cur stays valid for the termination below
-        sl.state = kNeedPop;
-      } else if (sl.state == kWaiting) {
-        if (sl.pend.valid) {
-          sl.cur = sl.pend;
-          sl.state = kRun;
-          sl.t = sl.cur.m;
-          sl.kdiv = 0;
-          sl.ediv = flash_div(0, sl.cur.T, sl.cur.Pe);
-          sl.eprev = -1;
-          sl.tmid = (sl.cur.m + sl.cur.n) / 2;
-        } else {
-          sl.state = kDone;
-        }
-      }
-      if (sl.state == kNeedPop) {
-        if (rank == 0) {
-          const unsigned long long k = atomicAdd(a.pop, 1ull);
-          PJob pj;
-          pj.valid = 0;
-          pj.b = pj.m = pj.n = pj.T = pj.Pe = pj.q_prev = pj.q_n = pj.pad = 0;
-          pj.s_prev = 0.f;
-          pj.e_off = pj.path_off = pj.aux_off = 0;
-          const bool from_tasks = kind == kJobSub || kind == kJobLeaf;
-          if (!from_tasks) {
-            if (k < (unsigned long long)a.order_count) {
-              const int b = a.order[a.order_begin + (int)k];
-              const Job jb = a.jobs[b];
-              pj.valid = 1;
-              pj.b = b;
-              pj.m = 0;
-              pj.n = jb.T - 1;
-              pj.T = jb.T;
-              pj.Pe = flash_pe(jb.T, a.P);
-              pj.e_off = jb.e_off;
-              pj.path_off = jb.path_off;
-              pj.aux_off = jb.aux_off;
-            }
-          } else if (k < (unsigned long long)*a.task_count) {
-            const Task tk = a.tasks[(a.task_first ? *a.task_first : 0) + (int64_t)k];
-            const Job jb = a.jobs[tk.b];
-            pj.valid = 1;
-            pj.b = tk.b;
-            pj.m = tk.m;
-            pj.n = tk.n;
-            pj.T = jb.T;
-            pj.e_off = jb.e_off;
-            pj.path_off = jb.path_off;
-            pj.aux_off = jb.aux_off;
-            pj.pad = tk.pad;
-            // states revealed by earlier levels; clamped so that no value can
-            // index shared memory outside the slab
-            const int qn = a.paths[jb.path_off + tk.n];
-            pj.q_n = (unsigned)qn < (unsigned)a.K ? qn : 0;
-            if (tk.m > 0) {
-              const int qp = a.paths[jb.path_off + tk.m - 1];
-              pj.q_prev = (unsigned)qp < (unsigned)a.K ? qp : 0;
-              pj.s_prev = a.sval[jb.aux_off + tk.m - 1];
-            }
-          }
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(&pj);
-          uint32_t* dst = reinterpret_cast<uint32_t*>(&sl.pend);
-          for (int w = 0; w < (int)(sizeof(PJob) / 4); ++w) {
-            dst[w] = src[w];
-            for (int r = 1; r < CL; ++r) dsmem_st_u32(dsmem_addr(dst + w, r), src[w]);
-          }
-        }
-        sl.state = kWaiting;
-      }
-      // this tick's descriptor of the slot
+    {
       TickDesc td;
       td.mode = 0;
       td.f_mid = td.f_snap = td.q_prev = td.first = td.sym = 0;
-      td.pad[0] = td.pad[1] = td.pad[2] = 0;
       td.s_prev = 0.f;
       td.psi_row = 0;
       td.erow = nullptr;
       td.snap_row = 0;
       td.map_row = -1;
-      if (sl.state == kRun) {
-        const int t = sl.t;
-        const PJob& jb = sl.cur;
-        td.mode = (t == jb.m) ? 1 : 2;
-        td.first = (t == 0);
-        td.q_prev = jb.q_prev;
-        td.s_prev = jb.s_prev;
-        td.psi_row = kind == kJobLeaf ? (int64_t)(jb.pad + t - jb.m - 1) * K : jb.aux_off + (int64_t)t * K;
-        if (a.emit == FV_EMIT_DENSE) td.erow = a.E + jb.e_off + (int64_t)t * K;
-        else td.sym = __ldg(a.obs + jb.e_off + t);
-        if (kind == kJobRoot) {
-          const int is_div = (t == sl.ediv);
-          if (sl.eprev >= 0) td.f_mid = (t == sl.eprev + 1) ? 1 : 2;
-          td.f_snap = is_div;
-          td.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)sl.kdiv * K;
-          td.map_row = (is_div && sl.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(sl.kdiv - 1) * K : -1;
-        } else if (kind == kJobSub) {
-          td.f_mid = (t == sl.tmid + 1) ? 1 : (t > sl.tmid + 1 ? 2 : 0);
-          td.f_snap = (t == sl.tmid);
+      int drawn_now = 0, live = 0, term = 0;
+      if (tid < S) {
+        Slot sl = slots[tid];
+        const bool done_before = sl.state == kDone;
+        if (done_before) {
+          // finished for good: its idle descriptor was stored when it ended
+          if (sl.term) slots[tid].term = 0;
+          sl.term = 0;
+        } else if (sl.state == kRun && sl.t + 1 < sl.ev) {
+          // plain step: nothing but t changes until step ev, so the
+          // descriptor advances by one row
+          td = tdesc[tid];
+          sl.t += 1;
+          sl.term = 0;
+          sl.drawn_now = 0;
+          td.psi_row += K;
+          if (a.emit == FV_EMIT_DENSE) td.erow += K;
+          else td.sym = __ldg(a.obs + sl.cur.e_off + sl.t);
+          live = !s_abort;
+        } else {
+          // advance the job that computed its step in the previous tick
+          if (sl.state == kRun) {
+            if (kind == kJobRoot && sl.t == sl.ediv) {
+              sl.eprev = sl.ediv;
+              sl.kdiv += 1;
+              sl.ediv = sl.kdiv < sl.cur.Pe ? flash_div(sl.kdiv, sl.cur.T, sl.cur.Pe) : 0x7fffffff;
+            }
+            sl.t += 1;
+          }
+          sl.term = 0;
+          sl.drawn_now = 0;
+          if (sl.state == kRun && sl.t > sl.cur.n) {
+            // the next job may start in this prologue: keep what the
+            // termination of this one reads
+            sl.term = 1;
+            SlotFin f;
+            f.b = sl.cur.b;
+            f.m = sl.cur.m;
+            f.n = sl.cur.n;
+            f.q_n = sl.cur.q_n;
+            f.path_off = sl.cur.path_off;
+            f.aux_off = sl.cur.aux_off;
+            s_fin[tid] = f;
+            sl.state = kIdle;
+          }
+          if (sl.state == kIdle && !sl.drawn) draw(sl, tick);
+          if (sl.state == kIdle && sl.drawn && tick >= sl.draw_tick + kLag) {
+            const PJob pj = s_pend[tid][(sl.ndraw - 1) & 1];
+            sl.drawn = 0;
+            if (pj.valid) {
+              sl.cur = pj;
+              sl.state = kRun;
+              sl.t = pj.m;
+              sl.kdiv = 0;
+              sl.ediv = flash_div(0, pj.T, pj.Pe);
+              sl.eprev = -1;
+              sl.tmid = (pj.m + pj.n) / 2;
+            } else {
+              sl.state = kDone;
+            }
+          }
+          // the next job is drawn one tick before this one's last step
+          if (sl.state == kRun && !sl.drawn && sl.cur.n - sl.t <= 1) draw(sl, tick);
+          drawn_now = sl.drawn_now;
+          live = (sl.state != kDone || sl.term) && !s_abort;
+          // this tick's descriptor of the slot
+          if (sl.state == kRun) {
+            const int t = sl.t;
+            const PJob& jb = sl.cur;
+            td.mode = (t == jb.m) ? 1 : 2;
+            td.first = (t == 0);
+            td.q_prev = jb.q_prev;
+            td.s_prev = jb.s_prev;
+            td.psi_row = kind == kJobLeaf ? (int64_t)(jb.pad + t - jb.m - 1) * K : jb.aux_off + (int64_t)t * K;
+            if (a.emit == FV_EMIT_DENSE) td.erow = a.E + jb.e_off + (int64_t)t * K;
+            else td.sym = __ldg(a.obs + jb.e_off + t);
+            if (kind == kJobRoot) {
+              const int is_div = (t == sl.ediv);
+              if (sl.eprev >= 0) td.f_mid = (t == sl.eprev + 1) ? 1 : 2;
+              td.f_snap = is_div;
+              td.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)sl.kdiv * K;
+              td.map_row = (is_div && sl.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(sl.kdiv - 1) * K : -1;
+            } else if (kind == kJobSub) {
+              // delta_{tmid} is complete in shared memory at the next tick,
+              // where rank 0 keeps it as the snapshot (t_mid < n)
+              td.f_mid = (t == sl.tmid + 1) ? 1 : (t > sl.tmid + 1 ? 2 : 0);
+              td.f_snap = (t == sl.tmid + 1);
+            }
+          }
+          // next step at which the descriptor changes other than by one row:
+          // the step after any non-steady one (first step, snapshot, map
+          // reset), the draw one step before the last, the next root
+          // division point and the sub snapshot step
+          if (sl.state == kRun) {
+            const int t = sl.t;
+            int ev = sl.cur.n - 1;
+            if (td.mode == 1 || td.f_snap || td.f_mid == 1) ev = min(ev, t + 1);
+            if (kind == kJobRoot && sl.ediv > t) ev = min(ev, sl.ediv);
+            if (kind == kJobSub && sl.tmid + 1 > t) ev = min(ev, sl.tmid + 1);
+            sl.ev = ev;
+          }
+        }
+        if (!done_before) {
+          tdesc[tid] = td;
+          slots[tid] = sl;
+        }
+        term = sl.term;
+      }
+      if (warp == 0) {
+        const bool own = tid < S;
+        const uint32_t act = __ballot_sync(0xffffffffu, own && td.mode != 0);
+        const uint32_t mid = __ballot_sync(0xffffffffu, own && td.f_mid != 0);
+        const uint32_t snp = __ballot_sync(0xffffffffu, own && kind == kJobSub && td.f_snap != 0);
+        const uint32_t drw = __ballot_sync(0xffffffffu, own && drawn_now);
+        const uint32_t trm = __ballot_sync(0xffffffffu, own && term);
+        if (lane == 0) {
+          s_info[tick & 1][0] = act;
+          s_info[tick & 1][1] = mid;
+          s_info[tick & 1][2] = snp;
+          s_info[tick & 1][3] = drw;
+          s_info[tick & 1][4] = trm;
         }
       }
-      tdesc[tid] = td;
+      if (!__syncthreads_or(live)) break;
     }
-    const int live = (tid < S) && (slots[tid].state != kDone || slots[tid].term);
-    if (!__syncthreads_or(live)) break;
-
-    // ---- termination of jobs that finished last tick (rank 0)
-    if (rank == 0) {
-      for (int s = warp; s < S; s += NW) {
-        if (!slots[s].term) continue;
-        const PJob& jb = slots[s].cur;
-        const float* dl = sD + (cur * S + s) * KPS;
-        if (kind == kJobVanilla) {
-          // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q]
-          float bv = -CUDART_INF_F;
-          int bi = 0x7fffffff;
-          for (int j = lane; j < K; j += 32) {
-            const float v = dl[j + ((j >> 5) << 2)];
-            if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
-          }
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-          }
-          if (lane == 0) {
-            a.qlast[jb.b] = bi;
-            a.scores[jb.b] = dl[bi + ((bi >> 5) << 2)];
-          }
-        } else if (kind == kJobSub && lane == 0) {
-          // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
-          const int tmid = (jb.m + jb.n) / 2;
-          int q = sMid[(cur * S + s) * KP + ((unsigned)jb.q_n < (unsigned)K ? jb.q_n : 0)];
-          q = (unsigned)q < (unsigned)K ? q : 0;
-          a.paths[jb.path_off + tmid] = q;
-          a.sval[jb.aux_off + tmid] = STREAM ? gSnap[s * KP + q] : sSnap[s * KP + q];
-        }
-      }
-    }
+    const uint32_t m_act = s_info[tick & 1][0], m_mid = s_info[tick & 1][1], m_snp = s_info[tick & 1][2];
+    const uint32_t m_drw = s_info[tick & 1][3], m_trm = s_info[tick & 1][4];
 
     // ---- prefetch this thread's emission scores (column jcol, OPT slots)
     float ev[OPT], pv[OPT];
@@ -451,6 +573,101 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       }
     }
 
+    // ---- streamed: the first ring stages of this tick's logA rows
+    const int sg = lane / LJ, jg = lane % LJ;
+    const int cg = warp % CG, rg = warp / CG;
+    float2* ring = STREAM ? reinterpret_cast<float2*>(sA) + warp * NST * 2 * WC : nullptr;
+    const float2* gsrc = STREAM ? a.Ap + (int64_t)(rg * C / 2) * a.ap_stride + j0 + cg * WC : nullptr;
+    constexpr int NIT = C / 4;
+    auto issue = [&](int it) {
+      float2* dst = ring + (it % NST) * 2 * WC;
+#pragma unroll
+      for (int u = 0; u < WC / 32; ++u) {
+        const int q = lane + 32 * u, pr = q / (WC / 2), c2 = (q % (WC / 2)) * 2;
+        cp_async16(dst + pr * WC + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
+      }
+    };
+    if constexpr (STREAM) {
+#pragma unroll
+      for (int k = 0; k < NST - 1; ++k) {
+        if (k < NIT) issue(k);
+        cp_async_commit();
+      }
+    }
+
+    // ---- multi-CTA clusters: wait until delta_{t-1} of every CTA is here;
+    // then rank 0 sends the jobs drawn in this tick's prologue
+    if constexpr (CL > 1 && kExch != 0) {
+      if (tick > 0) {
+        const uint32_t bar = smem_addr(&s_bar[(tick - 1) & 1]);
+        const uint32_t par = (uint32_t)((tick - 1) >> 1) & 1u;
+        if (!mbar_try_wait_cluster(bar, par)) {
+          const long long w0 = clock64();
+          while (!mbar_try_wait_cluster(bar, par)) {
+            if (clock64() - w0 > kClusterWaitCycles) {
+              set_status(a.hdr, FV_ETIMEOUT, 3);
+              s_abort = 1;
+              break;
+            }
+          }
+        }
+      }
+      if (rank == 0 && tid < S && ((m_drw >> tid) & 1u)) {
+        const PJob& pj = s_pend[tid][(slots[tid].ndraw - 1) & 1];
+        const uint4* src = reinterpret_cast<const uint4*>(&pj);
+#pragma unroll
+        for (int r = 1; r < CL; ++r) {
+          const uint32_t dst = dsmem_addr(&pj, r);
+#pragma unroll
+          for (int w = 0; w < (int)(sizeof(PJob) / 16); ++w) st_async_v4(dst + 16u * w, src[w], (tick & 1) ? pBar1[r] : pBar0[r]);
+        }
+      }
+    }
+
+    // ---- termination of jobs that finished last tick (rank 0)
+    if (rank == 0 && m_trm) {
+      for (int s = warp; s < S; s += NW) {
+        if (!((m_trm >> s) & 1u)) continue;
+        const SlotFin& fs = s_fin[s];
+        const float* dl = sD + (cur * S + s) * KPS;
+        if (kind == kJobVanilla) {
+          // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q]
+          float bv = -CUDART_INF_F;
+          int bi = 0x7fffffff;
+          for (int j = lane; j < K; j += 32) {
+            const float v = dl[j + ((j >> 5) << 2)];
+            if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+          }
+          if (lane == 0) {
+            a.qlast[fs.b] = bi;
+            a.scores[fs.b] = dl[bi + ((bi >> 5) << 2)];
+          }
+        } else if (kind == kJobSub && lane == 0) {
+          // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
+          const int tmid = (fs.m + fs.n) / 2;
+          int q = sMid[(cur * S + s) * KP + ((unsigned)fs.q_n < (unsigned)K ? fs.q_n : 0)];
+          q = (unsigned)q < (unsigned)K ? q : 0;
+          a.paths[fs.path_off + tmid] = q;
+          a.sval[fs.aux_off + tmid] = STREAM ? gSnap[s * KP + q] : sSnap[s * KP + q];
+        }
+      }
+    }
+
+    // ---- sub jobs: rank 0 keeps delta_{tmid} (all K states) as the snapshot
+    if (kind == kJobSub && rank == 0 && m_snp) {
+      for (int s = 0; s < S; ++s) {
+        if (!((m_snp >> s) & 1u)) continue;
+        const float* dl = sD + (cur * S + s) * KPS;
+        float* dst = STREAM ? gSnap + s * KP : sSnap + s * KP;
+        for (int j = tid; j < K; j += NT) dst[j] = dl[j + ((j >> 5) << 2)];
+      }
+    }
+
     // ---- main loop: value-only tropical product over this warp's C rows.
     // Per 4 rows a lane loads delta[4 slots][4 rows] and logA[4 rows][8
     // columns] as row pairs and issues one add.f32x2 + one 3-input max per
@@ -460,8 +677,6 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       // arrive 4 rows at a time through an NST-stage cp.async ring; chunk
       // winners (first chunk of CH rows reaching the running maximum) are
       // kept per output in registers
-      const int sg = lane / LJ, jg = lane % LJ;
-      const int cg = warp % CG, rg = warp / CG;
       float acc[4][TW], bst[4][TW];
       int bch[4][TW];
 #pragma unroll
@@ -473,22 +688,6 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           bch[x][y] = 0;
         }
       const int i0 = rg * C;
-      float2* ring = reinterpret_cast<float2*>(sA) + warp * NST * 2 * WC;
-      const float2* gsrc = a.Ap + (int64_t)(i0 / 2) * a.ap_stride + j0 + cg * WC;
-      constexpr int NIT = C / 4;
-      auto issue = [&](int it) {
-        float2* dst = ring + (it % NST) * 2 * WC;
-#pragma unroll
-        for (int u = 0; u < WC / 32; ++u) {
-          const int q = lane + 32 * u, pr = q / (WC / 2), c2 = (q % (WC / 2)) * 2;
-          cp_async16(dst + pr * WC + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
-        }
-      };
-#pragma unroll
-      for (int k = 0; k < NST - 1; ++k) {
-        if (k < NIT) issue(k);
-        cp_async_commit();
-      }
       const float* dbase0 = sD + (cur * S + sg * 4) * KPS;
 #pragma unroll 1
       for (int it = 0; it < NIT; ++it) {
@@ -540,9 +739,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           pc[2 * LJ * g + 1] = (uint8_t)bch[x][2 * g + 1];
         }
       }
-    } else     {
-      const int sg = lane / LJ, jg = lane % LJ;
-      const int cg = warp % CG, rg = warp / CG;
+    } else {
       float acc[4][TW];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
@@ -687,10 +884,9 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       }
     }
 
-    // ---- + E, per-kind bookkeeping, broadcast delta_t.  Global stores
+    // ---- + E, per-kind bookkeeping, delta_t to every CTA.  Global stores
     // (psi, root maps and snapshots) are kept in registers and issued after
-    // the cluster barrier's arrive, so its release only waits for the
-    // distributed shared memory writes.
+    // the exchange has been started.
     int st_arg[OPT], st_mid[OPT];
     float st_val[OPT];
     int64_t st_off[OPT], st_moff[OPT];
@@ -729,50 +925,98 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         const uint16_t mnew = td.f_mid == 1 ? (uint16_t)ag : sMid[(cur * S + s) * KP + ag];
         const int mo = (nxt * S + s) * KP + jcol;
         sMid[mo] = mnew;
-#pragma unroll
-        for (int rr = 0; rr < CL; ++rr)
-          if (rr != (int)rank) dsmem_st_u16(pMid[rr] + 2u * mo, mnew);
         st_mid[r] = mnew;
       }
-      if (td.f_snap) {
-        if (kind == kJobRoot) {
-          st_mask |= 1u << (2 * r + 1);
-          st_val[r] = dval;
-          st_off[r] = td.snap_row + jcol;
-          st_moff[r] = td.map_row >= 0 ? td.map_row + jcol : -1;
-        } else if constexpr (STREAM) {
-          gSnap[s * KP + jcol] = dval;
-        } else {
-          const int so = s * KP + jcol;
-          sSnap[so] = dval;
-#pragma unroll
-          for (int rr = 0; rr < CL; ++rr)
-            if (rr != (int)rank) dsmem_st_f32(pSnap[rr] + 4u * so, dval);
-        }
+      if (td.f_snap && kind == kJobRoot) {
+        st_mask |= 1u << (2 * r + 1);
+        st_val[r] = dval;
+        st_off[r] = td.snap_row + jcol;
+        st_moff[r] = td.map_row >= 0 ? td.map_row + jcol : -1;
       }
       sD[(nxt * S + s) * KPS + jcol + ((jcol >> 5) << 2)] = dval;
     }
-    // delta_t to the peers: the warp's 32 columns x OPT slots, re-read as
-    // 16-byte rows of 4 columns so each lane sends one vector per slot group
-    if (CL > 1) {
+    if constexpr (CL > 1 && kExch == 0) {
+      // delta_t (and MidState) to the other CTAs with plain remote stores,
+      // then the cluster barrier of this tick
       __syncwarp();
-      constexpr int LPS = 8;  // lanes per slot: 8 x 4 columns = the warp's 32 columns
       const int wcol = j0 + (tid % J) - lane;  // first column of this warp
 #pragma unroll
-      for (int r0 = 0; r0 < OPT; r0 += 32 / LPS) {
-        const int r = r0 + lane / LPS;
-        if (r >= OPT) break;
+      for (int r0 = 0; r0 < OPT; r0 += 4) {
+        const int r = r0 + lane / 8;
         const int s = s0 + r * SSTEP;
-        if (!tdesc[s].mode) continue;
-        const int c4 = wcol + 4 * (lane % LPS);
-        const int dof = (nxt * S + s) * KPS + c4 + ((c4 >> 5) << 2);
-        const float4 v = *reinterpret_cast<const float4*>(sD + dof);
+        if (r < OPT && ((m_act >> s) & 1u)) {
+          const int c4 = wcol + 4 * (lane % 8);
+          const int dof = (nxt * S + s) * KPS + c4 + ((c4 >> 5) << 2);
+          const float4 v = *reinterpret_cast<const float4*>(sD + dof);
 #pragma unroll
-        for (int rr = 0; rr < CL; ++rr)
-          if (rr != (int)rank) dsmem_st_v4f32(pD[rr] + 4u * dof, v.x, v.y, v.z, v.w);
+          for (int rr = 0; rr < CL; ++rr)
+            if (rr != (int)rank) dsmem_st_v4f32(pD[rr] + 4u * dof, v.x, v.y, v.z, v.w);
+        }
       }
+      if (m_mid) {
+#pragma unroll
+        for (int r0 = 0; r0 < OPT; r0 += 8) {
+          const int r = r0 + lane / 4;
+          const int s = s0 + r * SSTEP;
+          if (r < OPT && ((m_mid >> s) & 1u)) {
+            const int mo = (nxt * S + s) * KP + wcol + 8 * (lane % 4);
+            const float4 v = *reinterpret_cast<const float4*>(sMid + mo);
+#pragma unroll
+            for (int rr = 0; rr < CL; ++rr)
+              if (rr != (int)rank) dsmem_st_v4f32(pMid[rr] + 2u * mo, v.x, v.y, v.z, v.w);
+          }
+        }
+      }
+      cluster_arrive_release();
+    } else if constexpr (CL > 1) {
+      // this warp's local writes are done: arrive on this tick's barrier
+      // (warp 0 also announces the bytes the other CTAs will store here)
+      __syncwarp();
+      const int tb = tick & 1;
+      if (lane == 0) {
+        const uint32_t bar = smem_addr(&s_bar[tb]);
+        if (warp == 0) {
+          const uint32_t bytes =
+              (uint32_t)(CL - 1) * (uint32_t)(__popc(m_act) * J * 4 + __popc(m_mid) * J * 2) +
+              (rank != 0 ? (uint32_t)__popc(m_drw) * (uint32_t)sizeof(PJob) : 0u);
+          mbar_arrive_expect_tx(bar, bytes);
+        } else {
+          mbar_arrive(bar);
+        }
+      }
+      const int wcol = j0 + (tid % J) - lane;  // first column of this warp
+      // the warp's 32 columns of delta_t (and of MidState when set) to the
+      // other CTAs, 16 bytes per store
+#pragma unroll
+      for (int r0 = 0; r0 < OPT; r0 += 4) {
+        const int r = r0 + lane / 8;
+        const int s = s0 + r * SSTEP;
+        if (r < OPT && ((m_act >> s) & 1u)) {
+          const int c4 = wcol + 4 * (lane % 8);
+          const int dof = (nxt * S + s) * KPS + c4 + ((c4 >> 5) << 2);
+          const uint4 v = *reinterpret_cast<const uint4*>(sD + dof);
+#pragma unroll
+          for (int rr = 0; rr < CL; ++rr)
+            if (rr != (int)rank) st_async_v4(pD[rr] + 4u * dof, v, (tb ? pBar1[rr] : pBar0[rr]));
+        }
+      }
+      if (m_mid) {
+#pragma unroll
+        for (int r0 = 0; r0 < OPT; r0 += 8) {
+          const int r = r0 + lane / 4;
+          const int s = s0 + r * SSTEP;
+          if (r < OPT && ((m_mid >> s) & 1u)) {
+            const int mo = (nxt * S + s) * KP + wcol + 8 * (lane % 4);
+            const uint4 v = *reinterpret_cast<const uint4*>(sMid + mo);
+#pragma unroll
+            for (int rr = 0; rr < CL; ++rr)
+              if (rr != (int)rank) st_async_v4(pMid[rr] + 2u * mo, v, (tb ? pBar1[rr] : pBar0[rr]));
+          }
+        }
+      }
+    } else {
+      __syncthreads();
     }
-    if (CL > 1) cluster_arrive_release(); else __syncthreads();
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
       if (st_mask & (1u << (2 * r))) a.psi[st_off[r]] = (uint16_t)st_arg[r];
@@ -781,19 +1025,23 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         if (st_moff[r] >= 0) a.maps[st_moff[r]] = (uint16_t)st_mid[r];
       }
     }
-    if (CL > 1) cluster_wait_acquire();
-    if (tid < S && slots[tid].state == kRun) {
-      Slot& sl = slots[tid];
-      if (kind == kJobRoot && sl.t == sl.ediv) {
-        sl.eprev = sl.ediv;
-        sl.kdiv += 1;
-        sl.ediv = sl.kdiv < sl.cur.Pe ? flash_div(sl.kdiv, sl.cur.T, sl.cur.Pe) : 0x7fffffff;
-      }
-      sl.t += 1;
-    }
+    if constexpr (CL > 1 && kExch == 0) cluster_wait_acquire();
     cur = nxt;
   }
-  if (CL > 1) cluster_sync_all();
+  if constexpr (CL > 1) {
+    // the last tick's stores from the other CTAs land before anyone leaves
+    if (kExch != 0 && tick > 0) {
+      const uint32_t bar = smem_addr(&s_bar[(tick - 1) & 1]);
+      const uint32_t par = (uint32_t)((tick - 1) >> 1) & 1u;
+      const long long w0 = clock64();
+      while (!mbar_try_wait_cluster(bar, par))
+        if (clock64() - w0 > kClusterWaitCycles) {
+          set_status(a.hdr, FV_ETIMEOUT, 3);
+          break;
+        }
+    }
+    cluster_sync_all();
+  }
 }
 
 // ------------------------------------------------------------- backtrack
