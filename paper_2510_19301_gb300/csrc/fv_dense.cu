@@ -831,7 +831,9 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           float4 a4[2][CH / 4];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const float4* src = reinterpret_cast<const float4*>(a.wide_AT + (int64_t)jcol * KD + wbase[r0 + u]);
+            // the copy holds K columns: padded columns (unused outputs) are not read
+            const float4* src = reinterpret_cast<const float4*>(a.wide_AT + (int64_t)(jcol < K ? jcol : 0) * KD +
+                                                                wbase[r0 + u]);
 #pragma unroll
             for (int k = 0; k < CH / 4; ++k) a4[u][k] = __ldg(src + k);
           }
