@@ -336,6 +336,64 @@ def config4_train(fv, device, steps=10, warmup=3):
         torch.backends.cuda.matmul.allow_tf32 = prev_tf32
 
 
+def er_sweep(fv, device, reps=3):
+    """The paper's Erdos-Renyi family (Sec. VI): one sequence per point,
+    discrete emissions over 50 symbols; decode time (CUDA events, mean of
+    reps after warm-up) and decoder workspace per mode.  Sweeps: p at
+    K=T=512; K at p=0.253, T=512; T at p=0.253, K=512; beam width at K=2048,
+    T=512 (FLASH-BS P=16, with the relative score gap to the exact path)."""
+    import torch
+
+    import workloads as W
+    st = torch.cuda.current_stream()
+
+    def timed(d):
+        d(check=True)
+        for _ in range(2):
+            d.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            d.launch()
+        e1.record(st)
+        torch.cuda.synchronize()
+        assert d.device_status() == 0
+        return e0.elapsed_time(e1) / reps
+
+    def point(K, T, p, modes, seed):
+        c = W.erdos_renyi_case(K, T, p, seed=seed)
+        m = fv.Model(c["log_pi"], c["logA"], logB=c["logB"], device=device)
+        b = fv.Batch([T], obs=c["obs"], models=[m], device=device)
+        out = {"K": K, "T": T, "p": round(p, 6)}
+        ref = None
+        for name, kw in modes:
+            d = fv.Decoder([m], b, **kw)
+            row = {"ms": timed(d), "workspace_bytes": d.ws_bytes}
+            s = float(d.scores[0].item())
+            if ref is None:
+                ref = (d.paths[:T].clone(), s)
+            else:
+                row["same_path_as_vanilla"] = bool(torch.equal(ref[0], d.paths[:T]))
+                row["score_gap"] = abs(ref[1] - s) / abs(ref[1]) if ref[1] else 0.0
+            out[name] = row
+            del d
+        return out
+
+    def exact_modes(K):
+        return (("vanilla", {"mode": "vanilla"}), ("flash_P16", {"mode": "flash", "P": 16}),
+                ("flash_bs_P16_fullwidth", {"mode": "beam", "B": K, "P": 16}))
+
+    D = W.ER_DEFAULT
+    res = {"workload": "Erdos-Renyi HMMs (edge probability p, absent edges -inf), 50 symbols, one sequence",
+           "p_sweep": [point(D["K"], D["T"], p, exact_modes(D["K"]), 100 + i) for i, p in enumerate(W.ER_P_SWEEP)],
+           "K_sweep": [point(K, D["T"], D["p"], exact_modes(K), 200 + i) for i, K in enumerate(W.ER_SIZE_SWEEP)],
+           "T_sweep": [point(D["K"], T, D["p"], exact_modes(D["K"]), 300 + i) for i, T in enumerate(W.ER_SIZE_SWEEP)]}
+    res["B_sweep"] = point(2048, D["T"], D["p"], (("vanilla", {"mode": "vanilla"}),) + tuple(
+        (f"flash_bs_P16_B{B}", {"mode": "beam", "B": B, "P": 16}) for B in W.ER_BEAM_SWEEP), 400)
+    return res
+
+
 def config3_dense(fv, T, device, lib):
     """K=4096 dense (Dirichlet 0.1 rows), batch 8 of length T: vanilla with
     the full backpointer table against FLASH P=16 under a backpointer budget
@@ -646,6 +704,16 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_er_sweep():
+    import torch
+
+    import paper_2510_19301_gb300 as fv
+    torch.cuda.set_device(0)
+    res = er_sweep(fv, "cuda:0")
+    print(json.dumps({"metric": "Erdos-Renyi sweep: decode ms and workspace bytes per mode", "data": "synthetic",
+                      "n_gpus": 1, **res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -664,6 +732,8 @@ def main():
                     help="length of the K=4096 batch-8 run (0 = skip)")
     ap.add_argument("--c3s-T", dest="c3s_T", type=int, default=2000,
                     help="length of the K=65536 sparse beam runs (0 = skip)")
+    ap.add_argument("--er-sweep", dest="er_sweep", action="store_true",
+                    help="only the Erdos-Renyi sweep of the paper's synthetic family (one JSON line)")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=2.0,
                     help="arrival window of the serving run (60 = the full serving workload; 0 = skip)")
     args = ap.parse_args()
@@ -671,6 +741,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.er_sweep:
+        run_er_sweep()
     else:
         run_ours(args)
 

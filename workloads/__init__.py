@@ -21,8 +21,9 @@ Recipe (all FP32 after drawing in float64; logs taken in float64):
   {64,256,1024}, T = floor(exp(U(ln 100, ln 20000))), Dirichlet(1) model,
   log-softmax emissions, half exact and half beam (B=256).
 
-The erdos_renyi helper follows the paper's own synthetic family (edge
-probability p, missing edges are -inf).
+The erdos_renyi helpers follow the paper's own synthetic family (edge
+probability p, missing edges are -inf, discrete emissions over 50 symbols;
+``ER_*`` hold its default point and sweep ranges).
 """
 from __future__ import annotations
 
@@ -212,3 +213,24 @@ def erdos_renyi_model(K, p, seed):
         logA = np.log(w).astype(np.float32)
     log_pi = _log_dirichlet(rng, 1.0, (K,)).astype(np.float32)
     return log_pi, logA
+
+
+# The paper's default point and sweeps of its synthetic family (Sec. VI):
+# |O| = 50 symbols, p = 0.253, K = T = 512; p from 0.05 to 1 in steps of
+# x1.5, K and T from 32 to 2048, beam width from 1024 down to 32.
+ER_DEFAULT = dict(K=512, T=512, p=0.253, V=50)
+ER_P_SWEEP = tuple(min(1.0, 0.05 * 1.5 ** k) for k in range(9))  # 0.05 ... 1.0
+ER_SIZE_SWEEP = (32, 64, 128, 256, 512, 1024, 2048)
+ER_BEAM_SWEEP = (1024, 512, 256, 128, 64, 32)
+
+
+def erdos_renyi_case(K, T, p, V=50, seed=0):
+    """One HMM of the paper's Erdos-Renyi family and one observation
+    sequence sampled from it: transitions as in erdos_renyi_model (every
+    state keeps at least one out-edge), emission rows Dirichlet(1) over V
+    symbols, start log Dirichlet(1)."""
+    log_pi, logA = erdos_renyi_model(K, p, seed)
+    rng = np.random.default_rng(seed + 7)
+    logB = _log_dirichlet(rng, 1.0, (K, V)).astype(np.float32)
+    obs = sample_hmm_sequence(log_pi, logA, logB, T, rng)
+    return dict(K=K, T=T, p=p, V=V, log_pi=log_pi, logA=logA, logB=logB, obs=obs)
