@@ -696,6 +696,9 @@ def run_ours(args):
         out["config3_sparse"] = config3_sparse(fv, args.c3s_T, device, lib)
     if rank == 0 and args.serve_seconds > 0:
         out["serving"] = serving_run(args.serve_seconds)
+        # the same request mix at a rate below the measured capacity: the
+        # latencies are then service times, not queueing
+        out["serving_below_capacity"] = serving_run(5.0, rate=30.0)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
