@@ -225,6 +225,9 @@ def config1_latency(fv, device, iters=200):
     ref = None
     for name, kw in (("vanilla", {"mode": "vanilla"}), ("flash_P16", {"mode": "flash", "P": 16}),
                      ("beam_B16", {"mode": "beam", "B": 16, "P": 0})):
+        if name == "vanilla":
+            # engine configuration picked for this one-sequence request
+            out["engine_variant"] = int(fv.autotune([m], b, mode="vanilla")[0])
         d = fv.Decoder([m], b, **kw)
         with torch.cuda.stream(st):
             d(st, check=True)
@@ -283,6 +286,14 @@ def config4_train(fv, device, steps=10, warmup=3):
         logA = torch.from_numpy(w["logA"]).to(device).requires_grad_(True)
         lengths = w["T"]
 
+        # engine configuration of the K=128 class picked on this batch
+        with torch.no_grad():
+            E0 = X @ Wt.t() + bias
+        m0 = fv.Model(log_pi.detach(), logA.detach(), device=device)
+        tuned = int(fv.autotune([m0], fv.Batch(lengths, E=E0.reshape(-1), models=[m0], device=device),
+                                mode="flash", P=16)[0])
+        del E0
+
         def step():
             for p in (Wt, bias, log_pi, logA):
                 p.grad = None
@@ -329,7 +340,7 @@ def config4_train(fv, device, steps=10, warmup=3):
         return {"workload": "512 sequences, T in [20, 512], K=128 tags, 256 features; E = X W^T + b",
                 "ms_per_train_step": ms, "value": state_steps / (ms / 1e3), "unit": UNIT,
                 "decode_flash_P16_ms": dms, "backward_ms": bms, "loss": float(loss.item()),
-                "count_gradient_sums_exact": sums_exact,
+                "count_gradient_sums_exact": sums_exact, "engine_variant": tuned,
                 "note": "train step = emission GEMM + FLASH decode + path-count backward + GEMM gradients, "
                         "through torch.autograd (host work included)"}
     finally:
@@ -480,8 +491,10 @@ def serving_run(seconds, rate=2000.0, n_streams=128, max_wall=30.0):
     from paper_2510_19301_gb300.serve import GpuBackend, Server, poisson_requests
     reqs = poisson_requests(rate=rate, seconds=seconds, seed=6)
     be = GpuBackend(n_streams=n_streams)
+    variants = be.tune((64, 256, 1024))
     srv = Server(be, mem_budget_bytes=40 << 30, max_inflight=n_streams)
     rep = srv.run(reqs, max_wall=max(max_wall, 3 * seconds))
+    rep["engine_variants"] = variants
     rep.update({"arrival_rate_req_s": rate, "arrival_window_s": seconds, "offered": len(reqs),
                 "mix": "K uniform {64,256,1024}, T log-uniform [100,20000], 50% exact (vanilla) / "
                        "50% beam B=256",

@@ -194,6 +194,21 @@ class GpuBackend:
         return self.Decoder([m], b, mode=mode, P=req.P if req.mode != "exact" else 1,
                             B=req.B if req.mode == "beam" else 0)
 
+    def tune(self, Ks=(64, 256, 1024), T=2000):
+        """Engine configuration of each K class picked by the autotuner on one
+        representative request (a single sequence of T steps): requests here
+        are single sequences, not the full batches the defaults were chosen
+        for.  Results do not depend on the choice.  Returns {K: variant}."""
+        from . import autotune
+        chosen = {}
+        for K in Ks:
+            req = Request(rid=-1, K=int(K), T=int(T), seed=12345 + int(K))
+            log_pi, logA, E = self.make_inputs(req)
+            m = self.Model(log_pi, logA, device=self.device)
+            b = self.Batch([req.T], E=E.view(-1), models=[m], device=self.device)
+            chosen[int(K)] = int(autotune([m], b, mode="vanilla")[0])
+        return chosen
+
     def bytes_needed(self, req: Request):
         K, T = req.K, req.T
         inputs = 4 * (K * K + K + T * K)
