@@ -184,6 +184,9 @@ struct BeamSmem {
   int* red;           // [32]
   int* hist;          // [256]
   int* misc;          // [8]
+  uint32_t* lkey;     // [list_cap] ordered keys of this step's touched candidates (0: not finite)
+  int32_t* lj;        // [list_cap] their state ids, ascending
+  int nlist;          // entries in the list this step, -1 when the list is not in use
 };
 
 // Calls f(j) for every touched target j of this thread's contiguous range
@@ -204,16 +207,62 @@ __device__ inline void for_touched(const BeamSmem& sm, int j0, int j1, F&& f) {
   }
 }
 
-// Top-B of the touched candidates (finite only) -> beam buffer p, in id
-// order.  Returns the beam size (identical in every thread).  Each thread
-// owns a contiguous range of state ids, so the final compaction in thread
-// order is id order.
-__device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid) {
-  const int K = a.K, tid = threadIdx.x, lane = tid & 31;
-  const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int j0 = min(K, tid * per), j1 = min(K, j0 + per);
+// Small state spaces (K <= kBeamRankK, candidates in shared memory): thread
+// j owns candidate j, and its rank under (score desc, id asc) counts the
+// finite candidates ahead of it in one broadcast loop over the K scores;
+// the W first (every finite one when there are at most W) are written in id
+// order after one block scan.  Same result as the radix select below.
+constexpr int kBeamRankK = 256;
+
+__device__ int select_top_b_rank(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid) {
+  const int K = a.K, j = threadIdx.x;
+  const bool mine = j < K && ((sm.touched[j >> 5] >> (j & 31)) & 1u) && isfinite(S.cval[j]);
+  const float c = mine ? S.cval[j] : 0.f;
+  const uint32_t key = mine ? ord_key(c) : 0u;
+  const int n_fin = block_sum(mine ? 1 : 0, sm.red);
+  bool take = mine;
+  if (n_fin > W && mine) {
+    int rank = 0;
+    for (int w = 0; w < ((K + 31) >> 5); ++w) {
+      const uint32_t bits = sm.touched[w];
+#pragma unroll 8
+      for (int u = 0; u < 32; ++u) {
+        const int i = (w << 5) + u;
+        if (i >= K) break;
+        const float ci = S.cval[i];
+        const uint32_t ui = ord_key(ci);
+        const bool ahead = ((bits >> u) & 1u) && isfinite(ci) && (ui > key || (ui == key && i < j));
+        rank += ahead ? 1 : 0;
+      }
+    }
+    take = rank < W;
+  }
+  int tot;
+  const int o = block_scan(take ? 1 : 0, sm.red, &tot);
+  if (take) {
+    const int sl = S.cslot[j];
+    S.id[p][o] = j;
+    S.val[p][o] = c;
+    S.src[p][o] = sl;
+    if (need_mid == 1) S.mid[p][o] = S.id[p ^ 1][sl];
+    else if (need_mid == 2) S.mid[p][o] = S.mid[p ^ 1][sl];
+    else S.mid[p][o] = -1;
+  }
+  __syncthreads();
+  return tot;
+}
+
+// Top-B of the candidates (finite only) -> beam buffer p, in id order, by a
+// 4-pass MSB radix select on the ordered keys.  each(f) calls f(j, key) for
+// this thread's candidates in ascending id (key 0: not finite), and the
+// threads' candidate sets are ascending ranges in thread order, so the final
+// compaction in thread order is id order.  Returns the beam size (identical
+// in every thread).
+template <class Each>
+__device__ int select_core(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid, Each each) {
+  const int tid = threadIdx.x, lane = tid & 31;
   int cnt = 0;
-  for_touched(sm, j0, j1, [&](int j) { cnt += isfinite(S.cval[j]) ? 1 : 0; });
+  each([&](int, uint32_t u) { cnt += u ? 1 : 0; });
   const int n_fin = block_sum(cnt, sm.red);
   uint32_t thr = 0u;
   int need_eq = 0;
@@ -224,11 +273,8 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
     for (int shift = 24; shift >= 0; shift -= 8) {
       for (int k = tid; k < 256; k += blockDim.x) sm.hist[k] = 0;
       __syncthreads();
-      for_touched(sm, j0, j1, [&](int j) {
-        const float c = S.cval[j];
-        if (!isfinite(c)) return;
-        const uint32_t u = ord_key(c);
-        if ((u & mask) == prefix) atomicAdd(&sm.hist[(u >> shift) & 0xFFu], 1);
+      each([&](int, uint32_t u) {
+        if (u && (u & mask) == prefix) atomicAdd(&sm.hist[(u >> shift) & 0xFFu], 1);
       });
       __syncthreads();
       // the digit where the count from the top reaches `remaining`: lane l
@@ -268,12 +314,9 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
     need_eq = remaining;  // keys == thr to take, lowest ids first
   }
   int n_gt = 0, n_eq = 0;
-  for_touched(sm, j0, j1, [&](int j) {
-    const float c = S.cval[j];
-    if (!isfinite(c)) return;
-    if (all) { ++n_gt; return; }
-    const uint32_t u = ord_key(c);
-    if (u > thr) ++n_gt;
+  each([&](int, uint32_t u) {
+    if (!u) return;
+    if (all || u > thr) ++n_gt;
     else if (u == thr) ++n_eq;
   });
   int tot_eq, tot;
@@ -281,19 +324,14 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
   const int take_eq = min(max(need_eq - eq_before, 0), n_eq);
   const int pos = block_scan(n_gt + take_eq, sm.red, &tot);
   int o = pos, eq_seen = 0;
-  for_touched(sm, j0, j1, [&](int j) {
-    const float c = S.cval[j];
-    if (!isfinite(c)) return;
-    bool take = all;
-    if (!all) {
-      const uint32_t u = ord_key(c);
-      if (u > thr) take = true;
-      else if (u == thr) take = (eq_seen++ < take_eq);
-    }
+  each([&](int j, uint32_t u) {
+    if (!u) return;
+    bool take = all || u > thr;
+    if (!take && u == thr) take = (eq_seen++ < take_eq);
     if (!take) return;
     const int sl = S.cslot[j];
     S.id[p][o] = j;
-    S.val[p][o] = c;
+    S.val[p][o] = S.cval[j];
     S.src[p][o] = sl;
     if (need_mid == 1) S.mid[p][o] = S.id[p ^ 1][sl];
     else if (need_mid == 2) S.mid[p][o] = S.mid[p ^ 1][sl];
@@ -302,6 +340,31 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
   });
   __syncthreads();
   return tot;
+}
+
+__device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid) {
+  if (a.cand_smem && a.K <= kBeamRankK && a.K <= (int)blockDim.x) return select_top_b_rank(a, S, sm, p, W, need_mid);
+  if (sm.nlist >= 0) {
+    // this step's touched candidates are listed in shared memory: each
+    // thread takes a contiguous piece of the (id-ordered) list
+    const int n = sm.nlist, per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int e0 = min(n, (int)threadIdx.x * per), e1 = min(n, e0 + per);
+    const uint32_t* lkey = sm.lkey;
+    const int32_t* lj = sm.lj;
+    sm.nlist = -1;
+    return select_core(a, S, sm, p, W, need_mid, [&](auto&& f) {
+      for (int e = e0; e < e1; ++e) f(lj[e], lkey[e]);
+    });
+  }
+  const int K = a.K;
+  const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
+  return select_core(a, S, sm, p, W, need_mid, [&](auto&& f) {
+    for_touched(sm, j0, j1, [&](int j) {
+      const float c = S.cval[j];
+      f(j, isfinite(c) ? ord_key(c) : 0u);
+    });
+  });
 }
 
 // Clear the touched bitmap (and CSR keys of touched targets).
@@ -320,6 +383,7 @@ __device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamS
 // Candidates of step t from beam buffer p (size nb) into cval/cslot/touched.
 __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int p, int nb, int t) {
   const int K = a.K;
+  sm.nlist = -1;
   if (a.trans == FV_TRANS_DENSE) {
     // G threads per target (adjacent lanes) split the beam by slot
     // residue; the group keeps the highest value, the lowest slot on ties
@@ -378,6 +442,16 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
   __syncthreads();
   const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
   const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
+  // with a shared-memory list: this thread's touched targets go to
+  // positions [o, o + cnt) of it, so the list is in id order
+  int o = 0;
+  if (a.list_cap > 0) {
+    int cnt = 0;
+    for_touched(sm, j0, j1, [&](int) { ++cnt; });
+    int n;
+    o = block_scan(cnt, sm.red, &n);
+    sm.nlist = n <= a.list_cap ? n : -1;
+  }
   for_touched(sm, j0, j1, [&](int j) {
     const unsigned long long key = S.keys[j];
     const int sl = (int)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
@@ -385,8 +459,14 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
     // bijection away from zero); a zero is recomputed for its sign
     float m = ord_value((uint32_t)(key >> 32));
     if (m == 0.0f) m = __fadd_rn(S.val[p][sl], beam_csr_w(a, S.id[p][sl], j));
+    const float c = __fadd_rn(m, beam_emit(a, jb, t, j));
     S.cslot[j] = sl;
-    S.cval[j] = __fadd_rn(m, beam_emit(a, jb, t, j));
+    S.cval[j] = c;
+    if (sm.nlist >= 0) {
+      sm.lkey[o] = isfinite(c) ? ord_key(c) : 0u;
+      sm.lj[o] = j;
+      ++o;
+    }
   });
   __syncthreads();
 }
@@ -396,6 +476,7 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
 __device__ void beam_init(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int m, int q_prev,
                           float s_prev) {
   const int K = a.K;
+  sm.nlist = -1;
   if (m == 0 || a.trans == FV_TRANS_DENSE) {
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
       float c;
@@ -474,6 +555,13 @@ __global__ void __launch_bounds__(kBeamThreads, 1) beam_kernel(BeamArgs a) {
   sm.red = red;
   sm.hist = hist;
   sm.misc = misc;
+  sm.nlist = -1;
+  {
+    // the candidate list follows the bitmap, the beams and the candidates
+    uint32_t* lp = bsm + beam_bitmap_words(a.K) + (a.beam_smem ? 10 * a.Bcap : 0) + (a.cand_smem ? 2 * a.K : 0);
+    sm.lkey = lp;
+    sm.lj = reinterpret_cast<int32_t*>(lp + a.list_cap);
+  }
   if (a.hdr->status != 0) return;
   BeamScratch S = beam_scratch(a, bsm);
   const int K = a.K, nw = (K + 31) >> 5;
@@ -673,11 +761,35 @@ cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   if (b.beam_smem) smem += beam_bytes;
   b.cand_smem = smem + cand_bytes <= (size_t)208 * 1024;
   if (b.cand_smem) smem += cand_bytes;
+  // CSR with candidates in global memory: a shared-memory list of each
+  // step's touched candidates (8 bytes each) for the top-B select
+  // sized for B sources of 32 out-edges each (fewer if K is smaller); a
+  // step with more touched candidates uses the K-indexed arrays.  Not used
+  // when it would take most of the L1 cache the CSR gathers rely on.
+  b.list_cap = 0;
+  if (!b.cand_smem && a.trans != FV_TRANS_DENSE) {
+    size_t cap = (size_t)a.Bcap * 32;
+    if (cap > (size_t)a.K) cap = (size_t)a.K;
+    cap = (cap + 3) & ~(size_t)3;  // keeps the id array 16-byte aligned
+    if (smem + 8 * cap <= (size_t)160 * 1024) {
+      b.list_cap = (int32_t)cap;
+      smem += 8 * cap;
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = max_jobs < a.max_ctas ? max_jobs : a.max_ctas;
   if (grid < 1) return cudaSuccess;
-  beam_kernel<<<grid, kBeamThreads, smem, st>>>(b);
+  // small dense steps (beam x targets) use a smaller CTA: every step has
+  // several block-wide barriers and reductions whose cost grows with the
+  // thread count while the work does not
+  int threads = kBeamThreads;
+  if (a.trans == FV_TRANS_DENSE) {
+    const long long work = (long long)(a.Bcap < a.K ? a.Bcap : a.K) * a.K;
+    if (work <= 4096) threads = 128;
+    else if (work <= 16384) threads = 256;
+  }
+  beam_kernel<<<grid, threads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -135,6 +135,8 @@ struct BeamArgs {
   int32_t pe_cap;
   int32_t beam_smem;          // beams (both buffers + subtask snapshot) live in shared memory
   int32_t cand_smem;          // candidate values / sources live in shared memory
+  int32_t list_cap;           // CSR with candidates in global memory: entries of the shared-memory
+                              // list of a step's touched candidates (ordered key, state id); 0 = none
   WsHeader* hdr;
 };
 
