@@ -395,14 +395,14 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
       float best = -CUDART_INF_F;
       int sl = -1;
       if (j < K) {
-        // eight sources in flight per round; compared in slot order
+        // sixteen sources in flight per round; compared in slot order
         int k = sub;
-        for (; k + 7 * G < nb; k += 8 * G) {
-          float w[8];
+        for (; k + 15 * G < nb; k += 16 * G) {
+          float w[16];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) w[u] = __ldg(a.logA + (int64_t)S.id[p][k + u * G] * K + j);
+          for (int u = 0; u < 16; ++u) w[u] = __ldg(a.logA + (int64_t)S.id[p][k + u * G] * K + j);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < 16; ++u) {
             const float c = __fadd_rn(S.val[p][k + u * G], w[u]);
             if (sl < 0 || c > best) { best = c; sl = k + u * G; }
           }

@@ -16,6 +16,11 @@ def test_results_in_the_mix_equal_results_alone():
     reqs = poisson_requests(rate=2000.0, seconds=0.04, seed=11, Ks=(64, 256, 1024), tmin=20, tmax=600)
     assert len(reqs) > 30
     be = GpuBackend(n_streams=16, keep_results=True)
+    # engine configurations tuned on one short request per K class (results
+    # do not depend on them: the alone-decodes below use the same library)
+    tuned = be.tune((64, 256, 1024), T=200)
+    assert set(tuned) == {64, 256, 1024}
+    assert all(0 <= v < fv.set_engine_variant(K, v) for K, v in tuned.items())
     srv = Server(be, mem_budget_bytes=4 << 30, max_inflight=16)
     rep = srv.run(reqs)
     assert rep["failed"] == 0 and rep["requests"] == len(reqs)
