@@ -187,6 +187,7 @@ struct BeamSmem {
   uint32_t* lkey;     // [list_cap] ordered keys of this step's touched candidates (0: not finite)
   int32_t* lj;        // [list_cap] their state ids, ascending
   int nlist;          // entries in the list this step, -1 when the list is not in use
+  int nlist_used;     // entries listed in this step (kept for clearing the keys), -1 if none
 };
 
 // Calls f(j) for every touched target j of this thread's contiguous range
@@ -256,13 +257,15 @@ __device__ int select_top_b_rank(const BeamArgs& a, BeamScratch& S, BeamSmem& sm
 // 4-pass MSB radix select on the ordered keys.  each(f) calls f(j, key) for
 // this thread's candidates in ascending id (key 0: not finite), and the
 // threads' candidate sets are ascending ranges in thread order, so the final
-// compaction in thread order is id order.  Returns the beam size (identical
-// in every thread).
-template <class Each>
-__device__ int select_core(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid, Each each) {
+// compaction in thread order is id order.  any(f) visits the same
+// candidates split among the threads in any way (the counting passes do
+// not depend on order).  Returns the beam size (identical in every thread).
+template <class Any, class Each>
+__device__ int select_core(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid, Any any,
+                           Each each) {
   const int tid = threadIdx.x, lane = tid & 31;
   int cnt = 0;
-  each([&](int, uint32_t u) { cnt += u ? 1 : 0; });
+  any([&](int, uint32_t u) { cnt += u ? 1 : 0; });
   const int n_fin = block_sum(cnt, sm.red);
   uint32_t thr = 0u;
   int need_eq = 0;
@@ -273,7 +276,7 @@ __device__ int select_core(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int 
     for (int shift = 24; shift >= 0; shift -= 8) {
       for (int k = tid; k < 256; k += blockDim.x) sm.hist[k] = 0;
       __syncthreads();
-      each([&](int, uint32_t u) {
+      any([&](int, uint32_t u) {
         if (u && (u & mask) == prefix) atomicAdd(&sm.hist[(u >> shift) & 0xFFu], 1);
       });
       __syncthreads();
@@ -352,28 +355,43 @@ __device__ int select_top_b(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int
     const uint32_t* lkey = sm.lkey;
     const int32_t* lj = sm.lj;
     sm.nlist = -1;
-    return select_core(a, S, sm, p, W, need_mid, [&](auto&& f) {
+    auto list = [&](auto&& f) {
       for (int e = e0; e < e1; ++e) f(lj[e], lkey[e]);
-    });
+    };
+    return select_core(a, S, sm, p, W, need_mid, list, list);
   }
   const int K = a.K;
   const int per = (K + (int)blockDim.x - 1) / (int)blockDim.x;
   const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
-  return select_core(a, S, sm, p, W, need_mid, [&](auto&& f) {
-    for_touched(sm, j0, j1, [&](int j) {
-      const float c = S.cval[j];
-      f(j, isfinite(c) ? ord_key(c) : 0u);
-    });
-  });
+  // counting passes: ids strided over the block, so a warp reads
+  // consecutive candidates; the compaction keeps the contiguous ranges
+  return select_core(
+      a, S, sm, p, W, need_mid,
+      [&](auto&& f) {
+        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+          if (!((sm.touched[j >> 5] >> (j & 31)) & 1u)) continue;
+          const float c = S.cval[j];
+          f(j, isfinite(c) ? ord_key(c) : 0u);
+        }
+      },
+      [&](auto&& f) {
+        for_touched(sm, j0, j1, [&](int j) {
+          const float c = S.cval[j];
+          f(j, isfinite(c) ? ord_key(c) : 0u);
+        });
+      });
 }
 
 // Clear the touched bitmap (and CSR keys of touched targets).
 __device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm) {
   const int nw = (a.K + 31) >> 5;
   if (a.trans != FV_TRANS_DENSE) {
-    const int per = (a.K + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int j0 = min(a.K, (int)threadIdx.x * per), j1 = min(a.K, j0 + per);
-    for_touched(sm, j0, j1, [&](int j) { S.keys[j] = 0ull; });
+    if (sm.nlist_used > 0) {
+      for (int e = threadIdx.x; e < sm.nlist_used; e += blockDim.x) S.keys[sm.lj[e]] = 0ull;
+    } else {
+      for (int j = threadIdx.x; j < a.K; j += blockDim.x)
+        if ((sm.touched[j >> 5] >> (j & 31)) & 1u) S.keys[j] = 0ull;
+    }
     __syncthreads();
   }
   for (int w = threadIdx.x; w < nw; w += blockDim.x) sm.touched[w] = 0u;
@@ -384,6 +402,7 @@ __device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamS
 __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int p, int nb, int t) {
   const int K = a.K;
   sm.nlist = -1;
+  sm.nlist_used = -1;
   if (a.trans == FV_TRANS_DENSE) {
     // G threads per target (adjacent lanes) split the beam by slot
     // residue; the group keeps the highest value, the lowest slot on ties
@@ -452,7 +471,7 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
     o = block_scan(cnt, sm.red, &n);
     sm.nlist = n <= a.list_cap ? n : -1;
   }
-  for_touched(sm, j0, j1, [&](int j) {
+  auto cand = [&](int j) {
     const unsigned long long key = S.keys[j];
     const int sl = (int)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
     // the winning candidate is the key's value (the order map is a
@@ -462,12 +481,22 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
     const float c = __fadd_rn(m, beam_emit(a, jb, t, j));
     S.cslot[j] = sl;
     S.cval[j] = c;
-    if (sm.nlist >= 0) {
+    return c;
+  };
+  sm.nlist_used = sm.nlist;
+  if (sm.nlist >= 0) {
+    for_touched(sm, j0, j1, [&](int j) {
+      const float c = cand(j);
       sm.lkey[o] = isfinite(c) ? ord_key(c) : 0u;
       sm.lj[o] = j;
       ++o;
-    }
-  });
+    });
+  } else {
+    // no list: ids strided over the block, so a warp touches consecutive
+    // entries of the K-indexed arrays
+    for (int j = threadIdx.x; j < K; j += blockDim.x)
+      if ((sm.touched[j >> 5] >> (j & 31)) & 1u) cand(j);
+  }
   __syncthreads();
 }
 
@@ -477,6 +506,7 @@ __device__ void beam_init(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const
                           float s_prev) {
   const int K = a.K;
   sm.nlist = -1;
+  sm.nlist_used = -1;
   if (m == 0 || a.trans == FV_TRANS_DENSE) {
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
       float c;
@@ -556,6 +586,7 @@ __global__ void __launch_bounds__(kBeamThreads, 1) beam_kernel(BeamArgs a) {
   sm.hist = hist;
   sm.misc = misc;
   sm.nlist = -1;
+  sm.nlist_used = -1;
   {
     // the candidate list follows the bitmap, the beams and the candidates
     uint32_t* lp = bsm + beam_bitmap_words(a.K) + (a.beam_smem ? 10 * a.Bcap : 0) + (a.cand_smem ? 2 * a.K : 0);
