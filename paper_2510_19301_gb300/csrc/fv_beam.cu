@@ -697,6 +697,13 @@ __global__ void __launch_bounds__(kBeamThreads, 1) beam_kernel(BeamArgs a) {
           __syncthreads();
           break;
         }
+        // large CSR state spaces read this step's emission row at scattered
+        // targets: the next step's row goes to L2 while this one is used
+        if (a.trans != FV_TRANS_DENSE && a.emit == FV_EMIT_DENSE && threadIdx.x == 0 && t < n &&
+            (a.K & 3) == 0 && a.K >= 4096) {
+          const float* row = a.E + jb.e_off + (int64_t)(t + 1) * a.K;
+          if (((uintptr_t)row & 15u) == 0) prefetch_l2_bulk(row, (uint32_t)a.K * 4u);
+        }
         beam_candidates(a, S, sm, jb, p, nb, t);
         int need_mid = 0;
         if (a.kind == kJobRoot && eprev >= 0) need_mid = (t == eprev + 1) ? 1 : 2;

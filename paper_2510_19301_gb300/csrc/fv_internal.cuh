@@ -131,6 +131,12 @@ __device__ inline void st_async_v4(uint32_t addr, uint4 v, uint32_t remote_bar) 
 }
 __device__ inline void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
 
+// Asynchronous prefetch of `bytes` (multiple of 16, 16-byte aligned) from
+// global memory into L2; nothing waits for it.
+__device__ inline void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ inline float ld_nc(const float* p) { return __ldg(p); }
 
 // 16-byte asynchronous global -> shared copy (bypasses L1), and its groups.
