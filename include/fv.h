@@ -77,9 +77,11 @@ typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
  * fv_autotune / fv_set_engine_variant. */
 #define FV_NO_TUNE 0x8u
 /* Test hook for failure detection: the first CTA of the whole-GPU engine
- * (dense K > 1024) never publishes its step count, so every bounded wait on
- * it runs out (about one second); the call then reports FV_ETIMEOUT in the
- * status word and the CUDA context stays usable.  No other effect. */
+ * (dense K > 1024) never publishes its step count, and CTA 1 of every 4- or
+ * 8-CTA cluster of the streamed engine (256 < K <= 1024) withholds its
+ * arrivals on the delta exchange of the second tick, so the bounded waits on
+ * them run out (about one second each); the call then reports FV_ETIMEOUT in
+ * the status word and the CUDA context stays usable.  No other effect. */
 #define FV_TEST_WITHHOLD_STEP 0x80000000u
 
 /* One HMM, lambda = (pi, A, B) of Sec. III. K <= 65536 (backpointers are

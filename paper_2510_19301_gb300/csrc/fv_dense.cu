@@ -975,7 +975,10 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       // (warp 0 also announces the bytes the other CTAs will store here)
       __syncwarp();
       const int tb = tick & 1;
-      if (lane == 0) {
+      // test hook: CTA 1 of every cluster withholds its arrivals of the
+      // second tick, so the bounded waits run out (FV_TEST_WITHHOLD_STEP)
+      const bool withhold = a.wide_withhold && rank == 1 && tick == 1;
+      if (lane == 0 && !withhold) {
         const uint32_t bar = smem_addr(&s_bar[tb]);
         if (warp == 0) {
           const uint32_t bytes =

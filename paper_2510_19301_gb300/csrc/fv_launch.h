@@ -79,7 +79,8 @@ struct DenseArgs {
   uint32_t* wide_flags;
   const float* wide_AT;       // column-major copy of logA, AT[j * wide_lane_stride(K) + i] = A[i][j]
                               // (streamed and whole-GPU configurations: the exact re-scan reads it)
-  int32_t wide_withhold;      // test hook: CTA 0 never publishes its step count
+  int32_t wide_withhold;      // test hook: CTA 0 of the whole-GPU engine never publishes its step count;
+                              // CTA 1 of each 4- / 8-CTA cluster withholds its second-tick arrivals
   int32_t no_tune;            // use the default engine configuration, not the tuned one
   WsHeader* hdr;
 };

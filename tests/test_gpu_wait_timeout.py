@@ -1,8 +1,10 @@
-"""Failure detection of the whole-GPU engine without a GPU fault: with the
-test hook FV_TEST_WITHHOLD_STEP one CTA never publishes its step count, so
-the bounded waits of every CTA that depends on it run out (about a second).
-The call must report FV_ETIMEOUT through the workspace status word, leave
-the CUDA context usable, and the next ordinary call must decode exactly."""
+"""Failure detection without a GPU fault: with the test hook
+FV_TEST_WITHHOLD_STEP one CTA of the whole-GPU engine never publishes its
+step count, and one CTA of every 4- or 8-CTA cluster of the streamed engine
+withholds its arrivals on the delta exchange of the second tick, so the
+bounded waits that depend on them run out (about a second).  The call must
+report FV_ETIMEOUT through the workspace status word, leave the CUDA context
+usable, and the next ordinary call must decode exactly."""
 import numpy as np
 import pytest
 
@@ -13,12 +15,12 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_withheld_step_times_out_and_context_survives():
+@pytest.mark.parametrize("K", [1100, 300, 1000])
+def test_withheld_step_times_out_and_context_survives(K):
     import paper_2510_19301_gb300 as fv
     from paper_2510_19301_gb300 import _lib as L
     fv._lib.load(build_if_missing=True)
-    rng = np.random.default_rng(77)
-    K = 1100
+    rng = np.random.default_rng(77 + K)
     log_pi, logA = W.random_model(K, rng)
     lengths = [5, 9, 3]
     E_list = [W.gaussian_emissions(t, K, rng) for t in lengths]
