@@ -234,7 +234,11 @@ struct DenseCfg {
   static constexpr int OPT = S * J / NT;
   static constexpr int KP = KPM;          // rows, padded (-inf) to a fixed count
   static constexpr int C = KPM / RG;      // rows per row group
-  static constexpr int CH = STREAM ? 32 : C;  // rows per argmax chunk
+  // rows per argmax chunk: streamed engines track the first chunk reaching
+  // the maximum in the loop and re-scan that chunk from L2, so smaller
+  // chunks (measured: 8 rows for 4-CTA clusters, 16 for 8-CTA ones) trade
+  // a little loop work for a shorter re-scan
+  static constexpr int CH = STREAM ? (KPM <= 512 ? 8 : 16) : C;
   static constexpr int NST = KPM <= 512 ? 8 : 5;  // streamed: ring stages of 4 rows per warp
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
   static_assert(LJ * LS == 32 && LS * 4 == S && (TW == 8 || TW == 4), "lane tile is 4 sequences x TW columns");
