@@ -556,7 +556,11 @@ def run_ours(args):
     batch = fv.Batch(lengths, E=wl["E"].view(-1), models=[m], device=device)
     # engine configuration for this K class picked by the autotuner on this
     # very batch (all candidates give identical results)
-    chosen = fv.autotune([m], batch, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)
+    if args.engine_variant >= 0:
+        fv.set_engine_variant(K, args.engine_variant)
+        chosen = [args.engine_variant]
+    else:
+        chosen = fv.autotune([m], batch, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)
     dec = fv.Decoder([m], batch, mode=args.mode, P=args.P, B=args.B, mem_budget=args.budget)
     lib = fv._lib.load()
     state_steps = int(lengths.astype(np.int64).sum()) * K
@@ -748,6 +752,8 @@ def main():
                     help="length of the K=4096 batch-8 run (0 = skip)")
     ap.add_argument("--c3s-T", dest="c3s_T", type=int, default=2000,
                     help="length of the K=65536 sparse beam runs (0 = skip)")
+    ap.add_argument("--engine-variant", dest="engine_variant", type=int, default=-1,
+                    help="engine configuration of the K class (default: picked by the autotuner)")
     ap.add_argument("--er-sweep", dest="er_sweep", action="store_true",
                     help="only the Erdos-Renyi sweep of the paper's synthetic family (one JSON line)")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=2.0,

@@ -314,11 +314,19 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
       ap_bytes = std::max(ap_bytes, (size_t)(kpm / 2) * cols * 8);
       kpm_max = std::max(kpm_max, kpm);
     }
+    // resident K <= 256 configurations may keep their sub snapshots here too
+    bool resident_256 = false;
+    for (int m = 0; m < n_models; ++m) resident_256 |= models[m].K > 128 && models[m].K <= 256;
+    if (resident_256 && !ap_bytes) {
+      const int nsm = device_sm_count();
+      L.snapx = end;
+      end = align_up(L.snapx + sizeof(float) * (size_t)nsm * 1024);
+    }
     if (ap_bytes) {
       const int nsm = device_sm_count();
       L.ap = end;
       L.snapx = align_up(L.ap + ap_bytes);
-      end = align_up(L.snapx + sizeof(float) * (size_t)(nsm / 4 + 1) * 8 * kpm_max);
+      end = align_up(L.snapx + sizeof(float) * std::max((size_t)(nsm / 4 + 1) * 8 * kpm_max, (size_t)nsm * 1024));
       if (kmax > 1024) {
         L.wide = end;
         end = align_up(L.wide + wide_scratch_bytes(kmax, nsm));
@@ -674,6 +682,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
     {
       int kpm = 0, cols = 0;
       dense_stream_geometry(md.K, &kpm, &cols);
+      if (L.snapx) da.snap_scratch = reinterpret_cast<float*>(ws + L.snapx);
       if (kpm) {
         da.Ap = reinterpret_cast<const float2*>(ws + L.ap);
         da.ap_stride = cols;

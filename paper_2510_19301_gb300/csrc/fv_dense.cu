@@ -249,7 +249,13 @@ struct DenseCfg {
   // resident: logA slab [KP/2][J] float2; streamed: per-warp ring of NST
   // stages x 2 row pairs x J float2, plus the chunk id of each partial
   static constexpr size_t a_floats = STREAM ? (size_t)NW * NST * 4 * WC : (size_t)KP * J;
-  static constexpr size_t snap_floats = STREAM ? 0 : (size_t)S * KP;
+  // sub-job snapshots in shared memory unless they would not fit next to
+  // the rest (streamed engines and wide row-group splits keep them in the
+  // workspace, one row of KP floats per slot of each cluster)
+  static constexpr bool GSNAP =
+      STREAM || (a_floats + 2ull * S * KPS + (size_t)RG * S * J + (size_t)S * KP) * sizeof(float) +
+                        2ull * S * KP * sizeof(uint16_t) > (size_t)220 * 1024;
+  static constexpr size_t snap_floats = GSNAP ? 0 : (size_t)S * KP;
   static constexpr size_t smem_bytes =
       sizeof(float) * (a_floats + 2ull * S * KPS + (size_t)RG * S * J + snap_floats) +
       sizeof(uint16_t) * 2ull * S * KP + (STREAM ? (size_t)RG * S * J : 0);
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   uint8_t* sPC = reinterpret_cast<uint8_t*>(sMid + 2 * S * KP);            // streamed [RG][S][J] chunk
   const float2* sA2 = reinterpret_cast<const float2*>(sA);
   // streamed: global snapshot rows of this cluster's slots (sub jobs)
-  float* gSnap = STREAM ? a.snap_scratch + (size_t)(blockIdx.x / CL) * S * KP : nullptr;
+  float* gSnap = Cfg::GSNAP ? a.snap_scratch + (size_t)(blockIdx.x / CL) * S * KP : nullptr;
 
   const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
   const int j0 = (int)rank * J;
@@ -657,7 +663,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           int q = sMid[(cur * S + s) * KP + ((unsigned)fs.q_n < (unsigned)K ? fs.q_n : 0)];
           q = (unsigned)q < (unsigned)K ? q : 0;
           a.paths[fs.path_off + tmid] = q;
-          a.sval[fs.aux_off + tmid] = STREAM ? gSnap[s * KP + q] : sSnap[s * KP + q];
+          a.sval[fs.aux_off + tmid] = Cfg::GSNAP ? gSnap[s * KP + q] : sSnap[s * KP + q];
         }
       }
     }
@@ -667,7 +673,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       for (int s = 0; s < S; ++s) {
         if (!((m_snp >> s) & 1u)) continue;
         const float* dl = sD + (cur * S + s) * KPS;
-        float* dst = STREAM ? gSnap + s * KP : sSnap + s * KP;
+        float* dst = Cfg::GSNAP ? gSnap + s * KP : sSnap + s * KP;
         for (int j = tid; j < K; j += NT) dst[j] = dl[j + ((j >> 5) << 2)];
       }
     }
@@ -1300,7 +1306,7 @@ int dense_variants(int K) {
   switch (dense_k_class(K)) {
     case 0: return 3;
     case 1: return 2;
-    case 2: return 2;
+    case 2: return 3;
     case 3: return 2;
     case 4: return 2;
     default: return 1;
@@ -1328,6 +1334,7 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
   }
   if (a.K <= 256) {
+    if (v == 2) return launch_dense_cfg<128, 8, 16, 2, 256, false, 8>(a, max_clusters, st);
     if (v == 1) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
     return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);
   }
