@@ -33,10 +33,11 @@ UNIT = "state-steps/s"
 WORKLOAD = "batched-uneven: 1024 seqs, K=256 dense FP32, T~U[500,4000], E=log_softmax(N(0,1))"
 
 
-# DRAM bytes per state-step of dense_fwd_kernel (K=256, vanilla): reads of
-# E plus writes of psi, from one ncu capture (dram__bytes_read.sum +
+# DRAM bytes per state-step of dense_fwd_kernel (K=256, vanilla, the 16-warp
+# x 8-column configuration the autotuner picks on this batch): reads of E
+# plus writes of psi, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 128-sequence launch of this workload.
-DRAM_BYTES_PER_STATE_STEP = (280835072 + 109482240) / (271316 * 256)
+DRAM_BYTES_PER_STATE_STEP = (279438336 + 110472192) / (271316 * 256)
 
 
 def dist_env():
