@@ -51,7 +51,7 @@ typedef enum {
   FV_ENOMEM = 2,        /* workspace too small                             */
   FV_ECUDA = 3,         /* a CUDA runtime call failed                      */
   FV_ETIMEOUT = 4,      /* a bounded device wait ran out                   */
-  FV_EUNSUPPORTED = 5,  /* valid request this build does not implement     */
+  FV_EUNSUPPORTED = 5,  /* valid request the library does not implement    */
   FV_EINFEASIBLE = 6    /* no finite path (beam emptied / unreachable q_n) */
 } fv_status;
 
