@@ -86,12 +86,6 @@ __device__ inline void dsmem_st_v4f32(uint32_t addr, float x, float y, float z, 
 __device__ inline void dsmem_st_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
-__device__ inline void dsmem_st_u16(uint32_t addr, uint16_t v) {
-  asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
-}
-__device__ inline void dsmem_st_s64(uint32_t addr, long long v) {
-  asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
-}
 
 // mbarrier in this CTA's shared memory (32-bit shared-window addresses).
 __device__ inline uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -129,7 +123,6 @@ __device__ inline void st_async_v4(uint32_t addr, uint4 v, uint32_t remote_bar) 
                "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(remote_bar)
                : "memory");
 }
-__device__ inline void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
 
 // Asynchronous prefetch of `bytes` (multiple of 16, 16-byte aligned) from
 // global memory into L2; nothing waits for it.
@@ -137,7 +130,6 @@ __device__ inline void prefetch_l2_bulk(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ inline float ld_nc(const float* p) { return __ldg(p); }
 
 // 16-byte asynchronous global -> shared copy (bypasses L1), and its groups.
 __device__ inline void cp_async16(void* smem_dst, const void* gmem_src) {
