@@ -475,9 +475,18 @@ def config3_sparse(fv, T, device, lib):
         d = fv.Decoder([m], b, mode="beam", B=B, P=0)
         d(check=True)
         ms, fwd = time_decoder(d, 1, 0, lib)
+        eps = n * (T - 1) * B * 32 / (ms / 1e3)
+        hbm = peaks()[0].get("hbm_gbs", 6800.0)
+        # algorithmic bytes per edge relaxation: column index + edge weight,
+        # plus the emission score of its target (an upper bound: targets
+        # reached twice are read once)
+        gbs = 12.0 * eps / 1e9
         out[f"beam_B{B}"] = {"ms": ms, "value": n * T * K / (ms / 1e3), "unit": UNIT,
-                             "edge_relaxations_per_s": n * (T - 1) * B * 32 / (ms / 1e3),
-                             "workspace_bytes": d.ws_bytes}
+                             "edge_relaxations_per_s": eps, "workspace_bytes": d.ws_bytes,
+                             "roofline": {"bound": "latency", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                          "frac": gbs / hbm, "bytes_per_edge": 12,
+                                          "note": "one CTA per sequence (8 SMs busy): per-step latency, not "
+                                                  "bandwidth, bounds the step"}}
         del d
     del E
     torch.cuda.empty_cache()
