@@ -2,23 +2,27 @@
 // batched over uneven-length sequences in one persistent launch.
 //
 // Design (GB300-first):
-//  * A cluster of CL CTAs (one per SM) owns a model: CTA r keeps the column
-//    slab logA[:, rJ .. rJ+J) resident in shared memory for the whole
-//    launch (FP32, exact).  K <= CL*J.
+//  * A cluster of CL CTAs (one per SM) owns a model: CTA r computes the
+//    target columns [rJ, rJ+J).  K <= 256: its column slab of logA stays in
+//    shared memory for the whole launch (FP32, exact); 256 < K <= 1024: the
+//    slab streams from an L2-resident row-pair copy through a per-warp
+//    cp.async ring.
 //  * Each cluster runs S independent sequences ("slots") in lockstep: one
 //    tick computes one time step for every slot, so every logA element read
 //    from shared memory is reused S times from registers.
-//  * A tick is a small tropical GEMM: out[s][j] = max_i (delta[s][i] +
-//    logA[i][j]).  Warps split the i range; each lane holds a 4(s) x 8(j)
-//    register tile and issues one FADD + one FMNMX per cell.  The argmax is
-//    recovered exactly afterwards: the first warp whose partial maximum
-//    equals the overall maximum holds the lowest maximising index, which a
-//    short re-scan of that warp's rows finds (the value kept is the
-//    re-computed winning candidate, so ties and signed zeros follow the
-//    lowest-index rule bit for bit).
-//  * delta_t (and a bank-skewed transposed copy used by the re-scan) is
-//    broadcast to every CTA of the cluster through distributed shared memory;
-//    one cluster barrier per tick.
+//  * A tick is a small tropical product: out[s][j] = max_i (delta[s][i] +
+//    logA[i][j]).  Warps split the i range; each lane holds a 4(s) x 8(j) or
+//    4 x 4 register tile and issues one packed add.f32x2 and one 3-input max
+//    per two cells (value only).  The argmax is recovered exactly
+//    afterwards: the first row chunk whose partial maximum equals the
+//    overall maximum holds the lowest maximising index, which a short
+//    re-scan of that chunk finds (the value kept is the re-computed winning
+//    candidate, so ties and signed zeros follow the lowest-index rule bit
+//    for bit).
+//  * delta_t goes to every CTA of the cluster through distributed shared
+//    memory: one cluster barrier per tick for two CTAs, 16-byte st.async
+//    stores completing transaction bytes on the receiver's mbarrier (bounded
+//    waits) for four and eight.
 //  * Slots refill from a global work counter over a longest-first order, so
 //    uneven lengths keep every slot busy (continuous batching at the tick
 //    level).  psi is written as uint16 rows; the backtrack is a separate
