@@ -1,7 +1,8 @@
 // fv_beam.cu -- dynamic beam search (Sec. V-C) and FLASH-BS on GB300.
 //
-// One 1024-thread CTA runs one job at a time (a whole sequence, or one
-// Alg. 1 segment task) and pops the next job from a global counter.  A beam
+// One CTA (1024 threads; 128 or 256 for small dense steps) runs one job at
+// a time (a whole sequence, or one Alg. 1 segment task) and pops the next
+// job from a global counter.  A beam
 // is the top-B finite candidates under (score desc, state id asc); it is
 // kept sorted by state id so that the next step visits its sources in
 // ascending order.  Per step:
@@ -15,6 +16,8 @@
 //  * c_j = fl(M_j + E_t[j]); exact top-B: 4-pass MSB radix select on the
 //    order-preserving 32-bit key (-0 folded into +0), then the keys equal
 //    to the threshold are taken lowest id first (block scan in id order).
+//    K <= 256 with candidates in shared memory uses a rank select instead;
+//    CSR steps list their touched candidates in shared memory when they fit.
 // Beams and candidates live in shared memory when they fit (they are
 // re-read several times per step), else in a per-CTA slice of the
 // workspace; CSR scatter keys always live in the workspace.
