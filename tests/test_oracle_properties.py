@@ -76,3 +76,73 @@ def test_integer_ties_flash_equals_vanilla(case, P):
     pv, sv = oracle.viterbi(hmm, E)
     pf, sf, _ = oracle.flash(hmm, E, P)
     assert np.array_equal(pv, pf) and bits(sv) == bits(sf)
+
+
+def beam_restated(lp, A, E, B):
+    """The dynamic beam of Sec. V-C written out in Python: each step keeps
+    the top-B finite candidates under (score desc, state id asc); a target's
+    candidate comes from its best beam source (lowest id on equal scores),
+    and the final state is the best entry (highest score, lowest id)."""
+    T, K = E.shape
+    f32 = np.float32
+    c0 = [f32(lp[j] + E[0, j]) for j in range(K)]
+
+    def top(c):
+        fin = [j for j in range(K) if np.isfinite(c[j])]
+        fin.sort(key=lambda j: (-float(c[j]), j))
+        return sorted(fin[:B])
+
+    beam = top(c0)
+    vals = {j: c0[j] for j in beam}
+    back = []
+    for t in range(1, T):
+        if not beam:
+            return None
+        c, src = [f32(-np.inf)] * K, [None] * K
+        for j in range(K):
+            best, arg = None, None
+            for i in beam:  # ascending id
+                x = f32(vals[i] + A[i, j])
+                if best is None or x > best:
+                    best, arg = x, i
+            c[j] = f32(best + E[t, j])
+            src[j] = arg
+        beam = top(c)
+        vals = {j: c[j] for j in beam}
+        back.append({j: src[j] for j in beam})
+    if not beam:
+        return None
+    q = min(beam, key=lambda j: (-float(vals[j]), j))
+    score = vals[q]
+    path = [q]
+    for bp in reversed(back):
+        q = bp[q]
+        path.append(q)
+    return np.array(path[::-1], np.int32), score
+
+
+@settings(max_examples=150, deadline=None)
+@given(model_strategy(max_k=6, max_t=7), st.integers(1, 6))
+def test_beam_matches_restatement(case, B):
+    lp, A, E = case
+    K = lp.shape[0]
+    B = min(B, K)
+    hmm = oracle.HMM(lp, A)
+    ref = beam_restated(lp, A, E, B)
+    p, s, rc = oracle.beam(hmm, E, B)
+    if ref is None:
+        assert rc == 6
+        return
+    assert rc == 0 and np.array_equal(p, ref[0]) and bits(s) == bits(ref[1])
+
+
+@settings(max_examples=100, deadline=None)
+@given(model_strategy(max_k=5, max_t=9), st.integers(1, 9))
+def test_full_width_flash_bs_equals_vanilla(case, P):
+    lp, A, E = case
+    hmm = oracle.HMM(lp, A)
+    pv, sv = oracle.viterbi(hmm, E)
+    if not np.isfinite(sv):
+        return
+    pf, sf, _, rc = oracle.flash_bs(hmm, E, P, lp.shape[0])
+    assert rc == 0 and np.array_equal(pv, pf) and bits(sv) == bits(sf)
