@@ -146,3 +146,40 @@ def test_full_width_flash_bs_equals_vanilla(case, P):
         return
     pf, sf, _, rc = oracle.flash_bs(hmm, E, P, lp.shape[0])
     assert rc == 0 and np.array_equal(pv, pf) and bits(sv) == bits(sf)
+
+
+@st.composite
+def csr_case(d, max_k=6, max_t=7):
+    K = d(st.integers(1, max_k))
+    T = d(st.integers(1, max_t))
+    rng = np.random.default_rng(d(st.integers(0, 2 ** 31 - 1)))
+    lp = rng.standard_normal(K).astype(np.float32)
+    E = rng.standard_normal((T, K)).astype(np.float32)
+    row_ptr, col, val = [0], [], []
+    dense = np.full((K, K), -np.inf, np.float32)
+    for i in range(K):
+        succ = sorted(rng.choice(K, size=int(rng.integers(1, K + 1)), replace=False))
+        w = rng.standard_normal(len(succ)).astype(np.float32)
+        col += [int(j) for j in succ]
+        val += [float(x) for x in w]
+        dense[i, succ] = w
+        row_ptr.append(len(col))
+    return lp, E, np.array(row_ptr, np.int32), np.array(col, np.int32), np.array(val, np.float32), dense
+
+
+@settings(max_examples=100, deadline=None)
+@given(csr_case(), st.integers(1, 6))
+def test_csr_beam_matches_restatement_on_dense_equivalent(case, B):
+    lp, E, rp, col, val, dense = case
+    K = lp.shape[0]
+    B = min(B, K)
+    csr = oracle.HMM(lp, row_ptr=rp, col=col, val=val)
+    pv, sv = oracle.viterbi(csr, E)
+    pd, sd = oracle.viterbi(oracle.HMM(lp, dense), E)
+    assert np.array_equal(pv, pd) and bits(sv) == bits(sd)
+    ref = beam_restated(lp, dense, E, B)
+    p, s, rc = oracle.beam(csr, E, B)
+    if ref is None:
+        assert rc == 6
+        return
+    assert rc == 0 and np.array_equal(p, ref[0]) and bits(s) == bits(ref[1])
