@@ -148,9 +148,10 @@ def test_workspace_too_small_is_reported(fv):
 
 
 def test_config2_full_size_sampled(fv):
-    """The benchmark workload (1024 sequences, K=256, T ~ U[500,4000]) in the
-    benchmark's launch configuration; a sample of sequences (the longest,
-    the shortest, and random ones) is checked against the oracle."""
+    """The benchmark workload (1024 sequences, K=256, T ~ U[500,4000]) in
+    every engine configuration of its K class (the benchmark times the one
+    the autotuner picks); a sample of sequences (the longest, the shortest,
+    and random ones) is checked against the oracle."""
     K = 256
     log_pi, logA = W.config2_model()
     lengths = W.config2_lengths()
@@ -158,15 +159,21 @@ def test_config2_full_size_sampled(fv):
     E = W.gaussian_emissions_packed_device(e_total, K, seed=2)
     m = fv.Model(log_pi, logA)
     b = fv.Batch(lengths, E=E.view(-1), models=[m])
-    paths, scores = fv.decode([m], b)
     rng = np.random.default_rng(0)
     pick = sorted(set([int(np.argmax(lengths)), int(np.argmin(lengths))] + list(rng.choice(len(lengths), 14, replace=False))))
     e_off, p_off = W.packed_offsets(lengths, K)
     hmm = oracle.HMM(log_pi, logA)
     jobs = [E.view(-1)[e_off[i]:e_off[i] + lengths[i] * K].view(-1, K).cpu().numpy() for i in pick]
     res = oracle.map_sequences(lambda e: oracle.viterbi(hmm, e), jobs)
-    P = paths.cpu().numpy()
-    S = scores.cpu().numpy()
-    for i, (p, s) in zip(pick, res):
-        assert np.array_equal(P[p_off[i]:p_off[i] + lengths[i]], p), f"seq {i}"
-        assert bits(S[i]) == bits(s)
+    nv = fv.set_engine_variant(K, 0)
+    try:
+        for v in range(nv):
+            fv.set_engine_variant(K, v)
+            paths, scores = fv.decode([m], b)
+            P = paths.cpu().numpy()
+            S = scores.cpu().numpy()
+            for i, (p, s) in zip(pick, res):
+                assert np.array_equal(P[p_off[i]:p_off[i] + lengths[i]], p), f"variant {v} seq {i}"
+                assert bits(S[i]) == bits(s), f"variant {v} seq {i}"
+    finally:
+        fv.set_engine_variant(K, 0)
