@@ -406,6 +406,67 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
   const int K = a.K;
   sm.nlist = -1;
   sm.nlist_used = -1;
+  if (a.trans == FV_TRANS_DENSE && 2 * K > (int)blockDim.x && (K & 3) == 0 && ((uintptr_t)a.logA & 15u) == 0) {
+    // large K (more than one target per two threads): four adjacent targets
+    // per thread (16-byte loads of logA rows); G threads per group of four
+    // split the beam by slot residue and combine per target: highest value,
+    // lowest slot on ties.  Measured: 22% less time per candidate step at
+    // K=1024, B=256; slower for smaller K, where the scalar path below
+    // already splits each target's sources over several threads
+    const int K4 = K >> 2;
+    int G = 1;
+    while (G < 32 && 2 * G * K4 <= (int)blockDim.x) G *= 2;
+    const int groups = (int)blockDim.x / G, sub = (int)threadIdx.x % G;
+    for (int base = 0; base < K4; base += groups) {
+      const int j4 = base + (int)threadIdx.x / G;
+      float best[4];
+      int sl[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        best[c] = -CUDART_INF_F;
+        sl[c] = -1;
+      }
+      if (j4 < K4) {
+        auto take = [&](int k, float4 w) {
+          const float v = S.val[p][k];
+          const float c0 = __fadd_rn(v, w.x), c1 = __fadd_rn(v, w.y), c2 = __fadd_rn(v, w.z), c3 = __fadd_rn(v, w.w);
+          if (sl[0] < 0 || c0 > best[0]) { best[0] = c0; sl[0] = k; }
+          if (sl[1] < 0 || c1 > best[1]) { best[1] = c1; sl[1] = k; }
+          if (sl[2] < 0 || c2 > best[2]) { best[2] = c2; sl[2] = k; }
+          if (sl[3] < 0 || c3 > best[3]) { best[3] = c3; sl[3] = k; }
+        };
+        // eight sources in flight per round; compared in slot order
+        int k = sub;
+        for (; k + 7 * G < nb; k += 8 * G) {
+          float4 w[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            w[u] = __ldg(reinterpret_cast<const float4*>(a.logA + (int64_t)S.id[p][k + u * G] * K) + j4);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) take(k + u * G, w[u]);
+        }
+        for (; k < nb; k += G) take(k, __ldg(reinterpret_cast<const float4*>(a.logA + (int64_t)S.id[p][k] * K) + j4));
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float bv = best[c];
+        int bs = sl[c];
+        for (int o = 1; o < G; o <<= 1) {
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, o, G);
+          const int os = __shfl_xor_sync(0xffffffffu, bs, o, G);
+          if (os >= 0 && (bs < 0 || ov > bv || (ov == bv && os < bs))) { bv = ov; bs = os; }
+        }
+        const int j = 4 * j4 + c;
+        if (sub == 0 && j4 < K4) {
+          S.cslot[j] = bs;
+          S.cval[j] = __fadd_rn(bv, beam_emit(a, jb, t, j));
+          if (bs >= 0) atomicOr(&sm.touched[j >> 5], 1u << (j & 31));
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if (a.trans == FV_TRANS_DENSE) {
     // G threads per target (adjacent lanes) split the beam by slot
     // residue; the group keeps the highest value, the lowest slot on ties
