@@ -223,7 +223,7 @@ __device__ int select_top_b_rank(const BeamArgs& a, BeamScratch& S, BeamSmem& sm
   const bool mine = j < K && ((sm.touched[j >> 5] >> (j & 31)) & 1u) && isfinite(S.cval[j]);
   const float c = mine ? S.cval[j] : 0.f;
   const uint32_t key = mine ? ord_key(c) : 0u;
-  const int n_fin = block_sum(mine ? 1 : 0, sm.red);
+  const int n_fin = K <= W ? 0 : block_sum(mine ? 1 : 0, sm.red);  // every candidate fits when K <= W
   bool take = mine;
   if (n_fin > W && mine) {
     int rank = 0;
@@ -267,12 +267,15 @@ template <class Any, class Each>
 __device__ int select_core(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, int p, int W, int need_mid, Any any,
                            Each each) {
   const int tid = threadIdx.x, lane = tid & 31;
-  int cnt = 0;
-  any([&](int, uint32_t u) { cnt += u ? 1 : 0; });
-  const int n_fin = block_sum(cnt, sm.red);
+  // every candidate fits when K <= W; else count the finite ones
+  bool all = a.K <= W;
+  if (!all) {
+    int cnt = 0;
+    any([&](int, uint32_t u) { cnt += u ? 1 : 0; });
+    all = block_sum(cnt, sm.red) <= W;
+  }
   uint32_t thr = 0u;
   int need_eq = 0;
-  const bool all = n_fin <= W;
   if (!all) {
     uint32_t prefix = 0u, mask = 0u;
     int remaining = W;
