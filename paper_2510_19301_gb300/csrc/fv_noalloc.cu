@@ -32,7 +32,9 @@ void* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 // Device address of g_scratch on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The cache is keyed by the
+// device ordinal, so it belongs to the device's primary context (the one the
+// CUDA runtime uses) and does not survive cudaDeviceReset.
 fv_status scratch_on_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FV_ECUDA;
@@ -53,7 +55,11 @@ extern "C" fv_status fv_decode_noalloc(const fv_model* models, int32_t n_models,
                                        int32_t* paths_out, float* scores_out, fv_stream_t stream) {
   // Host lengths are required so the size check happens here, before
   // anything is enqueued.
-  if (!batch || !batch->T_host) return FV_EINVAL;
+  if (!batch || !batch->T_host || !models || n_models < 1) return FV_EINVAL;
+  // Dense transitions only: a CSR model would be decoded by the full-width
+  // beam, whose scratch this entry point does not promise to cover.
+  for (int32_t m = 0; m < n_models; ++m)
+    if (models[m].trans != FV_TRANS_DENSE) return FV_EUNSUPPORTED;
   fv_params p;
   p.mode = FV_VANILLA;
   p.P = 1;
@@ -70,4 +76,13 @@ extern "C" fv_status fv_decode_noalloc(const fv_model* models, int32_t n_models,
   // counters, job table) in its first kernel, so the previous call's
   // contents need no clearing here.
   return fv_decode(models, n_models, batch, &p, ws, kScratchBytes, paths_out, scores_out, stream);
+}
+
+extern "C" fv_status fv_decode_noalloc_status(fv_stream_t stream) {
+  // The status word sits at the start of the scratch (the workspace header),
+  // so the ordinary reader applies once the scratch's address is known.
+  void* ws = nullptr;
+  const fv_status s = scratch_on_current_device(&ws);
+  if (s != FV_OK) return s;
+  return fv_last_device_status(ws, stream);
 }

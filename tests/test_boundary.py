@@ -105,6 +105,21 @@ def test_argument_errors_return_at_once(lib):
     assert lib.fv_decode(m2, 2, ctypes.byref(b), ctypes.byref(p), ws, 1 << 20, FAKE, FAKE, None) == L.FV_EINVAL
 
 
+def test_noalloc_argument_refusals(lib):
+    """fv_decode_noalloc refuses, before any CUDA call: missing host lengths,
+    CSR models, and requests larger than its static scratch."""
+    m = (L.fv_model * 1)(_model())
+    b, T = _batch([4, 5])
+    b.T_host = None
+    assert lib.fv_decode_noalloc(m, 1, ctypes.byref(b), FAKE, FAKE, None) == L.FV_EINVAL
+    b, T = _batch([4, 5])
+    csr = (L.fv_model * 1)(_model(dense=False))
+    assert lib.fv_decode_noalloc(csr, 1, ctypes.byref(b), FAKE, FAKE, None) == L.FV_EUNSUPPORTED
+    big, Tb = _batch([40000])
+    m256 = (L.fv_model * 1)(_model(K=256))
+    assert lib.fv_decode_noalloc(m256, 1, ctypes.byref(big), FAKE, FAKE, None) == L.FV_ENOMEM
+
+
 def test_empty_batch_is_ok_without_device_work(lib):
     m = (L.fv_model * 1)(_model())
     b, _ = _batch([])
