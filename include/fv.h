@@ -247,10 +247,35 @@ int32_t fv_set_engine_variant(int32_t K, int32_t variant);
  * that device current) and caches it; make that first call before any
  * stream capture.  Every call shares the one array, so calls that overlap
  * on the GPU (two streams, two threads) race and corrupt each other's
- * results: serialise them.  Device-side errors are recorded inside the
- * shared scratch and are not reported by this entry point. */
+ * results: serialise them.  The address is cached per device ordinal, so
+ * the entry point works in the device's primary context (the one the CUDA
+ * runtime uses) and must not be called after cudaDeviceReset in the same
+ * process.  Models with CSR transitions are refused with FV_EUNSUPPORTED.
+ * Device-side errors (bad lengths on the device, a wait that ran out) are
+ * recorded in the shared scratch like fv_decode's; read them with
+ * fv_decode_noalloc_status. */
 fv_status fv_decode_noalloc(const fv_model* models, int32_t n_models, const fv_batch* batch,
                             int32_t* paths_out, float* scores_out, fv_stream_t stream);
+
+/* Status recorded on the device by the last fv_decode_noalloc call on the
+ * current device (synchronises `stream`, then copies the status word out of
+ * the static scratch; allocates nothing).  FV_OK before any call. */
+fv_status fv_decode_noalloc_status(fv_stream_t stream);
+
+/* Measured ceiling of the max-plus cell (not in the paper): runs the
+ * exact decoder's inner instruction pair -- one packed add.rn.f32x2 of two
+ * candidates delta[i] + logA[i][j] and one 3-input max.f32 into the running
+ * maximum, the cell of the tropical product of Sec. III-A -- on every SM
+ * (one CTA of 512 threads per SM; per thread and round, two source pairs
+ * read from shared memory, as the engines read delta, against 16 weight
+ * pairs in registers: 32 pairs, 64 cells, `iters` rounds), after one short
+ * warm-up launch.  Two forms of the adds are timed (one packed
+ * add.rn.f32x2, or two scalar add.rn.f32) and the faster is reported.
+ * Writes cells per second (CUDA events on `stream`), cells per clock per SM
+ * (clock64 of the first CTA; may be NULL) and the SM count (may be NULL).
+ * Synchronises `stream`; not capturable.  Allocates no device memory. */
+fv_status fv_maxplus_peak(int32_t iters, double* cells_per_s, double* cells_per_clk_sm,
+                          int32_t* sm_count, fv_stream_t stream);
 
 /* Library version string. */
 const char* fv_version(void);

@@ -306,3 +306,18 @@ def path_score(models, batch, paths, stream=None):
     if rc != L.FV_OK:
         raise FVError(rc, "fv_path_score")
     return out
+
+
+def maxplus_peak(iters=20000, stream=None):
+    """Measured max-plus ceiling of this GPU (fv_maxplus_peak): returns
+    (cells per second, cells per clock per SM, SM count)."""
+    lib = L.load()
+    cps = ctypes.c_double(0.0)
+    cpc = ctypes.c_double(0.0)
+    sms = ctypes.c_int32(0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.fv_maxplus_peak(int(iters), ctypes.byref(cps), ctypes.byref(cpc), ctypes.byref(sms),
+                             ctypes.c_void_p(st.cuda_stream))
+    if rc != L.FV_OK:
+        raise FVError(rc, "fv_maxplus_peak")
+    return cps.value, cpc.value, sms.value

@@ -122,10 +122,14 @@ def load(build_if_missing: bool = False):
     lib.fv_timing_read.restype = ctypes.c_int
     lib.fv_decode_noalloc.argtypes = [MP, i32, BP, P, P, P]
     lib.fv_decode_noalloc.restype = ctypes.c_int
+    lib.fv_decode_noalloc_status.argtypes = [P]
+    lib.fv_decode_noalloc_status.restype = ctypes.c_int
     lib.fv_autotune.argtypes = [MP, i32, BP, PP, P, sz, P, P, P, P]
     lib.fv_autotune.restype = ctypes.c_int
     lib.fv_set_engine_variant.argtypes = [i32, i32]
     lib.fv_set_engine_variant.restype = i32
+    lib.fv_maxplus_peak.argtypes = [i32, P, P, P, P]
+    lib.fv_maxplus_peak.restype = ctypes.c_int
     lib.fv_version.argtypes = []
     lib.fv_version.restype = ctypes.c_char_p
     _lib = lib
