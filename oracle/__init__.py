@@ -13,6 +13,9 @@ share no code.  Every function follows a passage of the paper:
 * ``beam``         -- dynamic beam search of Sec. V-C with per-step beam
                       backpointers (P = 0).
 * ``flash_bs``     -- FLASH-BS (Sec. V-C on top of Alg. 1/Alg. 2).
+* ``checkpoint``   -- Checkpoint Viterbi, the sqrt(T)-checkpoint baseline of
+                      Sec. II-A (forward pass keeping delta at checkpoints,
+                      then segments re-decoded latest first).
 * ``path_score``   -- log-likelihood of a path in forward order.
 * ``grad``         -- path-count gradient (not in the paper).
 
@@ -79,6 +82,10 @@ def _load():
         lib.orc_path_score.argtypes = [P, i32, P, P]
         lib.orc_path_score.restype = ctypes.c_float
         lib.orc_grad.argtypes = [i32, i32, P, P, P, P, P, P, P, P]
+        lib.orc_checkpoint.argtypes = [P, i32, P, i32, P, P, P, P]
+        lib.orc_checkpoint.restype = ctypes.c_int
+        lib.orc_checkpoint_count.argtypes = [i32, i32]
+        lib.orc_checkpoint_count.restype = i32
         lib.orc_split_points.argtypes = [i32, i32, P]
         lib.orc_split_points.restype = i32
         for f in (lib.orc_viterbi, lib.orc_flash, lib.orc_beam, lib.orc_flash_bs, lib.orc_grad):
@@ -199,6 +206,25 @@ def flash_bs(hmm: HMM, E, P: int, B: int, complete: bool = False):
     if rc not in (0, 6):
         raise RuntimeError(f"orc_flash_bs failed: {rc}")
     return path, score[0], int(reruns[0]), rc
+
+
+def checkpoint(hmm: HMM, E, P: int = 0):
+    """Checkpoint Viterbi with P checkpoints (P <= 0: ceil(sqrt(T))) ->
+    (path, score, n_checkpoints, largest segment in rows)."""
+    E = _E(E, hmm.K)
+    T = E.shape[0]
+    path = np.zeros(T, np.int32)
+    score = np.zeros(1, np.float32)
+    nc = np.zeros(1, np.int32)
+    mr = np.zeros(1, np.int32)
+    rc = _load().orc_checkpoint(hmm.ref, T, _ptr(E), int(P), _ptr(path), _ptr(score), _ptr(nc), _ptr(mr))
+    if rc:
+        raise RuntimeError(f"orc_checkpoint failed: {rc}")
+    return path, score[0], int(nc[0]), int(mr[0])
+
+
+def checkpoint_count(T: int, P: int = 0) -> int:
+    return int(_load().orc_checkpoint_count(int(T), int(P)))
 
 
 def path_score(hmm: HMM, E, path):

@@ -356,6 +356,86 @@ int orc_flash(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t 
 }
 
 /* ======================================================================== */
+/* Checkpoint Viterbi (the baseline of Sec. II-A, after Tarnas et al.):     */
+/* one forward pass keeps delta only at P' evenly spaced checkpoints        */
+/* (P' = ceil(sqrt(T)) by default, as the paper describes it), then the    */
+/* segments between checkpoints are decoded again from the last one,       */
+/* latest segment first, each with its own backpointer rows, and           */
+/* backtracked from the state already known at its end.  Checkpoints are   */
+/* the division points e_k of R3 (e_{P'-1} = T-1); segment k covers steps   */
+/* e_{k-1}+1 .. e_k and restarts from the stored delta_{e_{k-1}} (segment  */
+/* 0 from pi at t = 0).  The restarts are exact, so every backpointer      */
+/* equals the full table's.  Memory: P' rows of K floats plus one segment  */
+/* of at most ceil(T/P') rows.  *max_rows receives the largest segment.    */
+int32_t orc_checkpoint_count(int32_t T, int32_t P) {
+  if (T <= 1) return 1;
+  int32_t c = P;
+  if (c < 1) {
+    c = (int32_t)ceil(sqrt((double)T));
+    while ((int64_t)c * c < T) ++c;           /* exact integer ceiling */
+    while (c > 1 && (int64_t)(c - 1) * (c - 1) >= T) --c;
+  }
+  return c < T ? c : T;
+}
+
+int orc_checkpoint(const orc_model* m, int32_t T, const float* E, int32_t P, int32_t* path, float* score,
+                   int32_t* n_ckpt, int32_t* max_rows) {
+  if (!m || T < 1 || m->K < 1) return ORC_EINVAL;
+  const int32_t K = m->K, C = orc_checkpoint_count(T, P);
+  int32_t* e = malloc(sizeof(int32_t) * (size_t)C);
+  float* ck = malloc(sizeof(float) * (size_t)C * K);
+  float* d0 = malloc(sizeof(float) * K);
+  float* d1 = malloc(sizeof(float) * K);
+  float* best = malloc(sizeof(float) * K);
+  int32_t* junk = malloc(sizeof(int32_t) * K);
+  const int32_t seg_cap = (T + C - 1) / C + 1;
+  int32_t* psi = malloc(sizeof(int32_t) * (size_t)seg_cap * K);
+  if (!e || !ck || !d0 || !d1 || !best || !junk || !psi) {
+    free(e); free(ck); free(d0); free(d1); free(best); free(junk); free(psi);
+    return ORC_ENOMEM;
+  }
+  for (int32_t k = 0; k < C; ++k) e[k] = (int32_t)((((int64_t)k + 1) * T - 1) / C);
+  /* forward pass: delta kept only at the checkpoints */
+  int32_t kc = 0;
+  for (int32_t j = 0; j < K; ++j) d0[j] = m->log_pi[j] + E[j];
+  if (e[0] == 0) { memcpy(ck, d0, sizeof(float) * K); kc = 1; }
+  for (int32_t t = 1; t < T; ++t) {
+    exact_step(m, d0, E + (int64_t)t * K, best, d1, junk);
+    float* tmp = d0; d0 = d1; d1 = tmp;
+    if (kc < C && t == e[kc]) { memcpy(ck + (int64_t)kc * K, d0, sizeof(float) * K); ++kc; }
+  }
+  const float* last = ck + (int64_t)(C - 1) * K;
+  int32_t q = argmax_lowest(last, K);
+  *score = last[q];
+  path[T - 1] = q;
+  /* segments, latest first */
+  int32_t rows_max = 0;
+  for (int32_t k = C - 1; k >= 0; --k) {
+    const int32_t mm = (k == 0) ? 0 : e[k - 1], nn = e[k], rows = nn - mm;
+    if (rows > rows_max) rows_max = rows;
+    if (rows < 1) continue;
+    if (k == 0) {
+      for (int32_t j = 0; j < K; ++j) d0[j] = m->log_pi[j] + E[j];
+    } else {
+      memcpy(d0, ck + (int64_t)(k - 1) * K, sizeof(float) * K);
+    }
+    for (int32_t t = mm + 1; t <= nn; ++t) {
+      exact_step(m, d0, E + (int64_t)t * K, best, d1, psi + (int64_t)(t - mm - 1) * K);
+      float* tmp = d0; d0 = d1; d1 = tmp;
+    }
+    q = path[nn];
+    for (int32_t t = nn; t > mm; --t) {
+      q = psi[(int64_t)(t - mm - 1) * K + q];
+      path[t - 1] = q;
+    }
+  }
+  if (n_ckpt) *n_ckpt = C;
+  if (max_rows) *max_rows = rows_max;
+  free(e); free(ck); free(d0); free(d1); free(best); free(junk); free(psi);
+  return ORC_OK;
+}
+
+/* ======================================================================== */
 /* Dynamic beam search (Sec. V-C).  A beam is a set of (state, score)      */
 /* entries: the top-B finite candidates under (score desc, id asc) (R6).   */
 

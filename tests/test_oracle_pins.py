@@ -539,3 +539,49 @@ def test_grad_matches_float64_finite_differences(oracle):
         fd = (L(lp64, A64, Ep) - L(lp64, A64, Em)) / (2 * h)
         assert abs(fd - dE[off + t * K + j]) < 1e-5
         off += int(T[b]) * K
+
+
+# --------------------------------------------------------------------------
+# Checkpoint Viterbi (the sqrt(T)-checkpoint baseline of Sec. II-A).
+
+@pytest.mark.parametrize("K,T", [(2, 8), (3, 6), (4, 5), (4, 8), (1, 7), (3, 1)])
+def test_checkpoint_matches_brute_force(oracle, K, T):
+    """Score = the brute-force maximum bit for bit; on integer data the
+    path is the optimal one whose reversed sequence is smallest (the same
+    tie rule as the full table)."""
+    for seed in range(4):
+        for integer in (False, True):
+            log_pi, logA, E = W.random_small(K, T, seed=31 * seed + K, integer=integer, lo=-2, hi=2)
+            hmm = oracle.HMM(log_pi, logA)
+            paths, s = brute_scores(log_pi, logA, E)
+            for P in (0, 1, 2, 3, T):
+                path, score, _, _ = oracle.checkpoint(hmm, E, P)
+                assert bits(score) == bits(s.max())
+                match = np.all(paths == path[None, :], axis=1)
+                assert bits(s[match][0]) == bits(score)
+                if integer:
+                    assert np.array_equal(path, lex_min_reversed(paths[s == s.max()]))
+
+
+def test_checkpoint_equals_full_table_and_memory_bound(oracle):
+    """Restarting each segment from the exact stored delta reproduces every
+    backpointer of the full table, so the path and score are the full
+    table's for any checkpoint count (prime T, T below P, ties, -inf).
+    Memory: ceil(sqrt(T)) checkpoints by default and segments of at most
+    ceil(T/P') backpointer rows."""
+    import math
+    rng = np.random.default_rng(11)
+    for T in (1, 2, 3, 5, 16, 17, 31, 64, 97, 100, 257):
+        for trial in range(2):
+            K = int(rng.integers(1, 7))
+            log_pi, logA, E = W.random_small(K, T, seed=int(rng.integers(1 << 30)), integer=bool(trial),
+                                             lo=-3, hi=3, neg_inf_frac=0.2)
+            hmm = oracle.HMM(log_pi, logA)
+            pv, sv = oracle.viterbi(hmm, E)
+            for P in (0, 1, 2, 3, 7, T, T + 5):
+                path, score, nc, rows = oracle.checkpoint(hmm, E, P)
+                assert np.array_equal(path, pv), (T, P)
+                assert bits(score) == bits(sv)
+                want = (1 if T == 1 else min(T, math.isqrt(T - 1) + 1)) if P <= 0 else min(P, T)
+                assert nc == want == oracle.checkpoint_count(T, P)
+                assert rows <= -(-T // nc)
