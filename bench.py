@@ -435,7 +435,8 @@ def config3_dense(fv, T, device, lib):
            "state_steps": n * T * K}
     res = {}
     for name, kw in (("vanilla", {"mode": "vanilla"}),
-                     ("flash_P16_budget_1_16", {"mode": "flash", "P": 16, "mem_budget": table // 16})):
+                     ("flash_P16_budget_1_16", {"mode": "flash", "P": 16, "mem_budget": table // 16}),
+                     ("checkpoint_sqrtT", {"mode": "checkpoint", "P": 0})):
         d = fv.Decoder([m], b, **kw)
         d(check=True)
         ms, fwd = time_decoder(d, 1, 0, lib)
@@ -448,6 +449,10 @@ def config3_dense(fv, T, device, lib):
         torch.equal(pv, pf) and torch.equal(sv.view(torch.int32), sf.view(torch.int32)))
     out["flash_P16_budget_1_16"]["time_vs_vanilla"] = out["flash_P16_budget_1_16"]["ms"] / out["vanilla"]["ms"]
     out["flash_P16_budget_1_16"]["leaf_budget_bytes"] = table // 16
+    pc_, sc_ = res["checkpoint_sqrtT"].paths, res["checkpoint_sqrtT"].scores
+    out["checkpoint_sqrtT"]["bit_identical_to_vanilla"] = bool(
+        torch.equal(pv, pc_) and torch.equal(sv.view(torch.int32), sc_.view(torch.int32)))
+    out["checkpoint_sqrtT"]["time_vs_vanilla"] = out["checkpoint_sqrtT"]["ms"] / out["vanilla"]["ms"]
     out["full_backpointer_table_bytes"] = table
     cells = n * (T - 1) * K * K
     pk, _ = peaks()
@@ -695,6 +700,18 @@ def run_ours(args):
             "workspace_bytes": db.ws_bytes, "vanilla_workspace_bytes": dec.ws_bytes,
             "full_backpointer_table_bytes": table, "leaf_budget_bytes": table // 16}
         del db
+        # Checkpoint Viterbi (the sqrt(T)-checkpoint baseline of Sec. II-A)
+        dc = fv.Decoder([m], batch, mode="checkpoint", P=0)
+        dc(check=True)
+        cms, _ = time_decoder(dc, max(2, args.steps // 20), 2, lib)
+        modes["checkpoint_sqrtT"] = {
+            "value": state_steps / (cms / 1e3), "unit": UNIT, "ms_per_step": cms, "time_vs_vanilla": cms / ms,
+            "bit_identical_to_vanilla": bool(torch.equal(dec.paths, dc.paths) and torch.equal(
+                dec.scores.view(torch.int32), dc.scores.view(torch.int32))),
+            "workspace_bytes": dc.ws_bytes, "vanilla_workspace_bytes": dec.ws_bytes,
+            "note": "ceil(sqrt T) delta checkpoints per sequence, then one engine launch per checkpoint level "
+                    "re-decoding the latest segment of every sequence"}
+        del dc
         comp = per_sequence_comparator(fv, m, lengths, wl["E"], K, 32, device)
         comp["batched_over_per_sequence"] = value / world / comp["value"]
         modes["plain_per_sequence_gpu"] = comp

@@ -56,9 +56,10 @@ typedef enum {
 } fv_status;
 
 typedef enum {
-  FV_VANILLA = 0, /* full T x K uint16 backpointer table + backtrack (Sec. III-A) */
-  FV_FLASH = 1,   /* non-recursive D&C with MidState (Alg. 1, Alg. 2)            */
-  FV_BEAM = 2     /* dynamic beam (Sec. V-C); P >= 1 makes it FLASH-BS          */
+  FV_VANILLA = 0,   /* full T x K uint16 backpointer table + backtrack (Sec. III-A) */
+  FV_FLASH = 1,     /* non-recursive D&C with MidState (Alg. 1, Alg. 2)            */
+  FV_BEAM = 2,      /* dynamic beam (Sec. V-C); P >= 1 makes it FLASH-BS          */
+  FV_CHECKPOINT = 3 /* Checkpoint Viterbi, the baseline of Sec. II-A (see below)  */
 } fv_mode;
 
 typedef enum { FV_TRANS_DENSE = 0, FV_TRANS_CSR = 1 } fv_trans_kind;
@@ -135,6 +136,18 @@ typedef struct {
  * the known q*_n.  Those tasks run in waves whose tables fit the budget;
  * results are unchanged.  0 = pure divide and conquer.  The workspace grows
  * by at most the budget plus a small wave table.
+ *
+ * FV_CHECKPOINT (Checkpoint Viterbi, the comparison baseline of Sec. II-A):
+ * one forward pass keeps delta only at C checkpoints, C = ceil(sqrt(T))
+ * when P < 1, else min(P, T); checkpoint k is delta at e_k = floor(((k+1)T
+ * - 1)/C).  Then the segments between checkpoints are decoded again from
+ * the stored delta, latest first, each with its own backpointer rows, and
+ * backtracked from the state already known at the segment's end.  Paths
+ * and scores equal FV_VANILLA's bit for bit; per sequence the decoder
+ * holds C rows of K floats and one segment of at most ceil(T/C) rows of K
+ * uint16 (O(K sqrt T) instead of O(K T)), and decoding costs about two
+ * forward passes plus one engine launch per checkpoint level.  Dense
+ * transitions only (FV_EUNSUPPORTED for CSR), K <= 4096.
  *
  * Supported: FV_VANILLA and FV_FLASH on dense transitions need
  * K <= 4096 (FV_EUNSUPPORTED otherwise); K > 1024 runs one cooperative

@@ -22,7 +22,7 @@ from ._lib import FVError
 __all__ = ["Model", "Batch", "Decoder", "decode", "path_score", "workspace_size", "backward",
            "ViterbiScore", "FVError", "MODES", "autotune", "set_engine_variant"]
 
-MODES = {"vanilla": L.FV_VANILLA, "flash": L.FV_FLASH, "beam": L.FV_BEAM}
+MODES = {"vanilla": L.FV_VANILLA, "flash": L.FV_FLASH, "beam": L.FV_BEAM, "checkpoint": L.FV_CHECKPOINT}
 
 
 def _f32(x, device):

@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "fv.h")
 FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ETIMEOUT, FV_EUNSUPPORTED, FV_EINFEASIBLE = range(7)
 STATUS_NAMES = {0: "FV_OK", 1: "FV_EINVAL", 2: "FV_ENOMEM", 3: "FV_ECUDA", 4: "FV_ETIMEOUT",
                 5: "FV_EUNSUPPORTED", 6: "FV_EINFEASIBLE"}
-FV_VANILLA, FV_FLASH, FV_BEAM = 0, 1, 2
+FV_VANILLA, FV_FLASH, FV_BEAM, FV_CHECKPOINT = 0, 1, 2, 3
 FV_TRANS_DENSE, FV_TRANS_CSR = 0, 1
 FV_EMIT_DENSE, FV_EMIT_DISCRETE = 0, 1
 FV_COMPLETE_PRUNING = 0x1

@@ -255,7 +255,7 @@ int32_t beam_wcap(const fv_model* models, int32_t n_models, int32_t B) {
 // with P = 0, T*Wcap int32 state ids (a second area of the same size holds
 // the source slots).
 Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, int mode, const FlashPlan* fp,
-                  int32_t B = 0) {
+                  int32_t B = 0, int32_t ckpt_P = 0) {
   Layout L;
   memset(&L, 0, sizeof(L));
   const int32_t n = b->n_seq;
@@ -274,6 +274,7 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
     const uint64_t T = (uint64_t)b->T_host[i], K = (uint64_t)models[m].K;
     if (mode == FV_VANILLA) aux += (T * K + 7ull) & ~7ull;
     else if (beam0) aux += (T * (uint64_t)L.Wcap + 3ull) & ~3ull;
+    else if (mode == FV_CHECKPOINT) aux += ckpt_area((int32_t)T, ckpt_P, (int32_t)K);
     else aux += (T + 3ull) & ~3ull;
   }
   L.aux_elems = aux;
@@ -281,6 +282,13 @@ Layout layout_for(const fv_model* models, int32_t n_models, const fv_batch* b, i
   if (beam0) {
     L.aux2 = end;
     end = align_up(L.aux2 + 4 * (size_t)aux);
+  }
+  if (mode == FV_CHECKPOINT) {
+    // one segment list (a segment per sequence per level) and its count
+    L.list_cap = std::max<int64_t>(n, 1);
+    L.listA = end;
+    L.counts = align_up(L.listA + sizeof(Task) * (size_t)L.list_cap);
+    end = align_up(L.counts + 64);
   }
   if (fp) {
     L.list_cap = fp->list_cap;
@@ -588,7 +596,8 @@ size_t fv_workspace_size(const fv_model* models, int32_t n_models, const fv_batc
     return layout_for(models, n_models, batch, p->mode, &fp, p->B).total;
   }
   if (p->mode == FV_BEAM && p->B < 1) return 0;
-  return layout_for(models, n_models, batch, p->mode, nullptr, p->B).total;
+  if (p->mode != FV_VANILLA && p->mode != FV_BEAM && p->mode != FV_CHECKPOINT) return 0;
+  return layout_for(models, n_models, batch, p->mode, nullptr, p->B, p->P).total;
 }
 
 fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* batch, const fv_params* p_in,
@@ -603,7 +612,8 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   const fv_params* p = &pq;
   if (!workspace || ws_bytes < 4096 || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1))) return FV_EINVAL;
   if (batch->n_seq > 0 && (!paths_out || !scores_out)) return FV_EINVAL;
-  if (p->mode != FV_VANILLA && p->mode != FV_FLASH && p->mode != FV_BEAM) return FV_EINVAL;
+  if (p->mode != FV_VANILLA && p->mode != FV_FLASH && p->mode != FV_BEAM && p->mode != FV_CHECKPOINT)
+    return FV_EINVAL;
   if (p->mode == FV_FLASH && p->P < 1) return FV_EINVAL;
   if (p->mode == FV_BEAM && (p->B < 1 || p->P < 0)) return FV_EINVAL;
   if (p->mode != FV_VANILLA && !batch->T_host) return FV_EINVAL;  // task levels are planned from host lengths
@@ -617,7 +627,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   if (tasks)
     fp = plan_flash(models, n_models, batch, p->P, p->mode == FV_FLASH ? p->mem_budget_bytes : 0,
                     (p->flags & FV_NO_SORT) != 0);
-  const Layout L = layout_for(models, n_models, batch, p->mode, tasks ? &fp : nullptr, p->B);
+  const Layout L = layout_for(models, n_models, batch, p->mode, tasks ? &fp : nullptr, p->B, p->P);
   if (batch->T_host && ws_bytes < L.total) return FV_ENOMEM;
   if (ws_bytes < L.aux) return FV_ENOMEM;
   const uint64_t cap = (ws_bytes - L.aux) / (p->mode == FV_VANILLA ? 2 : 4);
@@ -639,8 +649,11 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
   pa.n_seq = n;
   pa.n_models = n_models;
   for (int m = 0; m < n_models; ++m) pa.mk.K[m] = models[m].K;
-  pa.aux_kind = p->mode == FV_VANILLA ? 1 : ((p->mode == FV_BEAM && !tasks) ? 3 : 2);
-  pa.aux_mult = L.Wcap;
+  pa.aux_kind = p->mode == FV_VANILLA      ? 1
+                : p->mode == FV_CHECKPOINT ? 4
+                : (p->mode == FV_BEAM && !tasks) ? 3
+                                                 : 2;
+  pa.aux_mult = p->mode == FV_CHECKPOINT ? p->P : L.Wcap;
   pa.jobs = jobs;
   pa.hdr = hdr;
   pa.aux_cap = p->mode == FV_VANILLA ? cap : L.aux_elems;
@@ -710,6 +723,44 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
         da.wide_AT = at;
         if (launch_wide_transpose(md.logA, md.K, at, st) != cudaSuccess) return FV_ECUDA;
       }
+    }
+    if (p->mode == FV_CHECKPOINT) {
+      // Checkpoint Viterbi: forward pass keeping the checkpoints, last
+      // state and score, then one level of segments per checkpoint,
+      // latest segment first
+      float* area = reinterpret_cast<float*>(ws + L.aux);
+      Task* list = reinterpret_cast<Task*>(ws + L.listA);
+      int32_t* count = reinterpret_cast<int32_t*>(ws + L.counts);
+      int32_t levels = 0;
+      for (int i = 0; i < n; ++i)
+        if ((batch->model_host ? batch->model_host[i] : 0) == m)
+          levels = std::max(levels, ckpt_count(batch->T_host[i], p->P));
+      da.ckpt = 1;
+      da.snaps = area;
+      da.psi = reinterpret_cast<uint16_t*>(area);
+      da.kind = kJobRoot;
+      timed_begin(st);
+      if (m > 0 && launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
+      if (launch_dense_forward(da, 0, st) != cudaSuccess) return FV_ECUDA;
+      if (launch_ckpt_resolve(jobs, order, R.begin[m], R.count[m], md.K, p->P, area, paths_out, scores_out, hdr,
+                              st) != cudaSuccess)
+        return FV_ECUDA;
+      for (int lvl = 0; lvl < levels; ++lvl) {
+        if (launch_ckpt_tasks(jobs, order, R.begin[m], R.count[m], p->P, lvl, list, count, st) != cudaSuccess)
+          return FV_ECUDA;
+        if (launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
+        da.kind = kJobLeaf;
+        da.tasks = list;
+        da.task_count = count;
+        da.task_first = nullptr;
+        da.max_jobs = R.count[m];
+        if (launch_dense_forward(da, 0, st) != cudaSuccess) return FV_ECUDA;
+        if (launch_ckpt_backtrack(list, count, R.count[m], jobs, md.K, p->P, reinterpret_cast<uint16_t*>(area),
+                                  paths_out, hdr, st) != cudaSuccess)
+          return FV_ECUDA;
+      }
+      timed_end(st);
+      continue;
     }
     if (p->mode == FV_VANILLA) {
       uint16_t* psi = reinterpret_cast<uint16_t*>(ws + L.aux);

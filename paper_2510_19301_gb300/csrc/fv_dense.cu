@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(1024) prep_kernel(PrepArgs p) {
       if (p.aux_kind == 1) need = ((unsigned long long)T * K + 7ull) & ~7ull;
       else if (p.aux_kind == 2) need = ((unsigned long long)T + 3ull) & ~3ull;
       else if (p.aux_kind == 3) need = ((unsigned long long)T * (unsigned long long)p.aux_mult + 3ull) & ~3ull;
+      else if (p.aux_kind == 4) need = ckpt_area(T, p.aux_mult, (int32_t)K);
     }
     // block exclusive scan of need
     unsigned long long x = need;
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         pj.m = 0;
         pj.n = jb.T - 1;
         pj.T = jb.T;
-        pj.Pe = flash_pe(jb.T, a.P);
+        pj.Pe = a.ckpt ? ckpt_count(jb.T, a.P) : flash_pe(jb.T, a.P);
         pj.e_off = jb.e_off;
         pj.path_off = jb.path_off;
         pj.aux_off = jb.aux_off;
@@ -364,12 +365,17 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       pj.pad = tk.pad;
       // states revealed by earlier levels; clamped so that no value can
       // index shared memory outside the slab
-      const int qn = a.paths[jb.path_off + tk.n];
-      pj.q_n = (unsigned)qn < (unsigned)a.K ? qn : 0;
-      if (tk.m > 0) {
-        const int qp = a.paths[jb.path_off + tk.m - 1];
-        pj.q_prev = (unsigned)qp < (unsigned)a.K ? qp : 0;
-        pj.s_prev = a.sval[jb.aux_off + tk.m - 1];
+      if (a.ckpt) {
+        // checkpoint segment: restarts from checkpoint tk.pad (or from pi)
+        pj.Pe = ckpt_count(jb.T, a.P);
+      } else {
+        const int qn = a.paths[jb.path_off + tk.n];
+        pj.q_n = (unsigned)qn < (unsigned)a.K ? qn : 0;
+        if (tk.m > 0) {
+          const int qp = a.paths[jb.path_off + tk.m - 1];
+          pj.q_prev = (unsigned)qp < (unsigned)a.K ? qp : 0;
+          pj.s_prev = a.sval[jb.aux_off + tk.m - 1];
+        }
       }
     }
     return pj;
@@ -517,15 +523,26 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
             td.first = (t == 0);
             td.q_prev = jb.q_prev;
             td.s_prev = jb.s_prev;
-            td.psi_row = kind == kJobLeaf ? (int64_t)(jb.pad + t - jb.m - 1) * K : jb.aux_off + (int64_t)t * K;
+            td.psi_row = kind != kJobLeaf ? jb.aux_off + (int64_t)t * K
+                         : a.ckpt ? 2 * (jb.aux_off + (int64_t)jb.Pe * K) + (int64_t)(t - jb.m - 1) * K
+                                  : (int64_t)(jb.pad + t - jb.m - 1) * K;
             if (a.emit == FV_EMIT_DENSE) td.erow = a.E + jb.e_off + (int64_t)t * K;
             else td.sym = __ldg(a.obs + jb.e_off + t);
             if (kind == kJobRoot) {
               const int is_div = (t == sl.ediv);
-              if (sl.eprev >= 0) td.f_mid = (t == sl.eprev + 1) ? 1 : 2;
               td.f_snap = is_div;
-              td.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)sl.kdiv * K;
-              td.map_row = (is_div && sl.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(sl.kdiv - 1) * K : -1;
+              if (a.ckpt) {
+                // checkpoints only: delta_t at division point kdiv
+                td.snap_row = jb.aux_off + (int64_t)sl.kdiv * K;
+              } else {
+                if (sl.eprev >= 0) td.f_mid = (t == sl.eprev + 1) ? 1 : 2;
+                td.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)sl.kdiv * K;
+                td.map_row =
+                    (is_div && sl.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(sl.kdiv - 1) * K : -1;
+              }
+            } else if (kind == kJobLeaf && a.ckpt && jb.pad >= 0) {
+              // checkpoint segment: the restart reads checkpoint jb.pad
+              td.snap_row = jb.aux_off + (int64_t)jb.pad * K;
             } else if (kind == kJobSub) {
               // delta_{tmid} is complete in shared memory at the next tick,
               // where rank 0 keeps it as the snapshot (t_mid < n)
@@ -922,6 +939,9 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       if (td.mode == 1) {
         if (td.first) {
           dval = __fadd_rn(pv[r], ev[r]);
+        } else if (a.ckpt) {
+          // checkpoint restart: delta_m exactly as the forward pass stored it
+          dval = __ldg(a.snaps + td.snap_row + jcol);
         } else {
           // pruned start (Sec. V-B.2): only transitions out of q*_{m-1}
           const float av = STREAM ? __ldg(a.logA + (int64_t)td.q_prev * K + jcol)

@@ -326,6 +326,138 @@ cudaError_t launch_leaf_backtrack(const Task* tasks, const int32_t* wave_first, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- Checkpoint Viterbi
+// The baseline of Sec. II-A: the forward pass (engine, kJobRoot with ckpt)
+// keeps delta at C checkpoints e_k in each sequence's area; then segment k
+// (steps e_{k-1}+1 .. e_k) is decoded again from checkpoint k-1 (segment 0
+// from pi), latest segment first, one segment per sequence per level, and
+// backtracked from the state already known at its end.
+
+// One warp per sequence: q_{T-1} = lowest argmax of the last checkpoint
+// (delta_{T-1}), its score and the path's last state.
+__global__ void __launch_bounds__(128) ckpt_resolve_kernel(const Job* jobs, const int32_t* order, int32_t begin,
+                                                           int32_t count, int32_t K, int32_t P, const float* area,
+                                                           int32_t* paths, float* scores, const WsHeader* hdr) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (idx >= count || hdr->status != 0) return;
+  const int b = order[begin + idx];
+  const Job jb = jobs[b];
+  const float* last = area + jb.aux_off + (int64_t)(ckpt_count(jb.T, P) - 1) * K;
+  float bv = -CUDART_INF_F;
+  int bi = 0x7fffffff;
+  for (int j = lane; j < K; j += 32) {
+    const float v = last[j];
+    if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+  }
+  if (lane == 0) {
+    scores[b] = last[bi];
+    paths[jb.path_off + jb.T - 1] = bi;
+  }
+}
+
+// Level `level` of the segment lists: for every sequence (in `order`) with
+// more than `level` checkpoints, its segment C-1-level (one CTA, block scan
+// so the list keeps the sequence order).  Segments without a step (segment
+// 0 when e_0 = 0) are left out: their state is written by the next
+// segment's backtrack.
+__global__ void __launch_bounds__(1024) ckpt_tasks_kernel(const Job* jobs, const int32_t* order, int32_t begin,
+                                                          int32_t count, int32_t P, int32_t level, Task* out,
+                                                          int32_t* out_count) {
+  __shared__ int warp_sum[32];
+  __shared__ int carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < count; base += blockDim.x) {
+    const int i = base + tid;
+    Task tk;
+    int has = 0;
+    if (i < count) {
+      const int b = order[begin + i];
+      const Job jb = jobs[b];
+      const int C = ckpt_count(jb.T, P), k = C - 1 - level;
+      if (k >= 0) {
+        tk.b = b;
+        tk.m = k == 0 ? 0 : div_of(k - 1, jb.T, C);
+        tk.n = div_of(k, jb.T, C);
+        tk.pad = k - 1;
+        has = tk.n > tk.m;
+      }
+    }
+    int x = has;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int v = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      warp_sum[lane] = v;
+    }
+    __syncthreads();
+    const int pos = carry + (w ? warp_sum[w - 1] : 0) + x - has;
+    if (has) out[pos] = tk;
+    __syncthreads();
+    if (tid == blockDim.x - 1) carry = pos + has;
+    __syncthreads();
+  }
+  if (tid == 0) *out_count = carry;
+}
+
+// One thread per segment: follow q_{t-1} = psi_t[q_t] from the known
+// q_n through the segment's rows (stored after the checkpoints).
+__global__ void __launch_bounds__(128) ckpt_backtrack_kernel(const Task* tasks, const int32_t* count,
+                                                             const Job* jobs, int32_t K, int32_t P,
+                                                             const uint16_t* area16, int32_t* paths,
+                                                             const WsHeader* hdr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (hdr->status != 0 || idx >= *count) return;
+  const Task tk = tasks[idx];
+  const Job jb = jobs[tk.b];
+  int32_t* path = paths + jb.path_off;
+  const uint16_t* base = area16 + 2 * (jb.aux_off + (int64_t)ckpt_count(jb.T, P) * K);
+  int q = path[tk.n];
+  q = (unsigned)q < (unsigned)K ? q : 0;
+  for (int t = tk.n; t > tk.m; --t) {
+    q = base[(int64_t)(t - tk.m - 1) * K + q];
+    q = q < K ? q : 0;
+    path[t - 1] = q;
+  }
+}
+
+cudaError_t launch_ckpt_resolve(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t K,
+                                int32_t P, const float* area, int32_t* paths, float* scores, const WsHeader* hdr,
+                                cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  ckpt_resolve_kernel<<<(count + 3) / 4, 128, 0, st>>>(jobs, order, begin, count, K, P, area, paths, scores, hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ckpt_tasks(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                              int32_t level, Task* out, int32_t* out_count, cudaStream_t st) {
+  ckpt_tasks_kernel<<<1, 1024, 0, st>>>(jobs, order, begin, count, P, level, out, out_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ckpt_backtrack(const Task* tasks, const int32_t* count, int32_t max_count, const Job* jobs,
+                                  int32_t K, int32_t P, const uint16_t* area16, int32_t* paths, const WsHeader* hdr,
+                                  cudaStream_t st) {
+  if (max_count <= 0) return cudaSuccess;
+  ckpt_backtrack_kernel<<<(max_count + 127) / 128, 128, 0, st>>>(tasks, count, jobs, K, P, area16, paths, hdr);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ FV_CHECKED
 __device__ inline bool bad_score(float x) { return isnan(x) || (isinf(x) && x > 0.f); }
 

@@ -1,6 +1,7 @@
 // fv_launch.h -- host-side launchers shared between libfv translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "fv_internal.cuh"
@@ -15,7 +16,8 @@ struct PrepArgs {
   int32_t n_seq;
   int32_t n_models;
   ModelK mk;
-  int32_t aux_kind;  // 0: none, 1: T*K uint16 backpointers, 2: T floats, 3: T*aux_mult int32
+  int32_t aux_kind;  // 0: none, 1: T*K uint16 backpointers, 2: T floats, 3: T*aux_mult int32,
+                     // 4: Checkpoint Viterbi area (ckpt_area with P = aux_mult)
   int32_t aux_mult;
   Job* jobs;
   WsHeader* hdr;
@@ -32,10 +34,37 @@ enum JobKind : int32_t {
                     // (budget leaf); rows start at element task.pad * K of the leaf area
 };
 
-// One divide-and-conquer task (Alg. 1 tuple) of sequence b.
+// One divide-and-conquer task (Alg. 1 tuple) of sequence b.  Checkpoint
+// segments use the same tuple: (m, n) is the segment and pad the index of
+// the checkpoint it restarts from (-1: it starts at t = 0 from pi).
 struct Task {
   int32_t b, m, n, pad;
 };
+
+// Checkpoint Viterbi (the sqrt(T)-checkpoint baseline of Sec. II-A): the
+// number C of checkpoints of a length-T sequence, ceil(sqrt(T)) unless P >= 1
+// asks for P, at most T.  Checkpoint k is delta at the division point
+// e_k = floor(((k+1)T - 1) / C) (e_{C-1} = T - 1); segment k covers steps
+// e_{k-1}+1 .. e_k.
+__host__ __device__ inline int32_t ckpt_count(int32_t T, int32_t P) {
+  if (T <= 1) return 1;
+  int32_t c = P;
+  if (c < 1) {
+    c = (int32_t)sqrtf((float)T);
+    while ((int64_t)c * c < T) ++c;
+    while (c > 1 && (int64_t)(c - 1) * (c - 1) >= T) --c;
+  }
+  return c < T ? c : T;
+}
+// Backpointer rows of the longest segment (upper bound ceil(T / C)).
+__host__ __device__ inline int32_t ckpt_rows(int32_t T, int32_t C) { return (T + C - 1) / C; }
+// Per-sequence area of Checkpoint Viterbi, in 4-byte elements: C rows of
+// K floats (the checkpoints), then ckpt_rows rows of K uint16 backpointers
+// (one segment at a time), rounded to 16 bytes.
+__host__ __device__ inline uint64_t ckpt_area(int32_t T, int32_t P, int32_t K) {
+  const uint64_t C = (uint64_t)ckpt_count(T, P), R = (uint64_t)ckpt_rows(T, (int32_t)C);
+  return (C * (uint64_t)K + (R * (uint64_t)K + 1ull) / 2ull + 3ull) & ~3ull;
+}
 
 struct DenseArgs {
   int32_t K;
@@ -68,6 +97,11 @@ struct DenseArgs {
   int64_t snap_stride;
   int32_t P;
   int32_t complete;           // offset-0 (complete pruning) start for subtasks
+  // Checkpoint Viterbi: kJobRoot keeps only delta at the checkpoints (no
+  // MidState), in the sequence's area at job.aux_off of `snaps`; kJobLeaf
+  // restarts segment tasks from those checkpoints and writes the segment's
+  // backpointer rows after them (`psi` = the same area as uint16)
+  int32_t ckpt;
   const float2* Ap;           // streamed configurations: row-pair copy of logA
   int64_t ap_stride;          // float2 per row pair of Ap
   float* snap_scratch;        // streamed configurations: sub snapshots [clusters][S][rows]
@@ -189,6 +223,16 @@ cudaError_t launch_level1_tasks(const Job* jobs, const int32_t* order, int32_t b
 cudaError_t launch_child_tasks(const Task* in, const int32_t* in_count, int32_t max_in, Task* out,
                                int32_t* out_count, ScanTmp tmp, unsigned long long* pop_reset, cudaStream_t st);
 cudaError_t launch_reset(unsigned long long* pop, cudaStream_t st);
+// Checkpoint Viterbi (fv_flash.cu): q_{T-1} and the score from the last
+// checkpoint; the segment list of one level; the segment backtrack.
+cudaError_t launch_ckpt_resolve(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t K,
+                                int32_t P, const float* area, int32_t* paths, float* scores, const WsHeader* hdr,
+                                cudaStream_t st);
+cudaError_t launch_ckpt_tasks(const Job* jobs, const int32_t* order, int32_t begin, int32_t count, int32_t P,
+                              int32_t level, Task* out, int32_t* out_count, cudaStream_t st);
+cudaError_t launch_ckpt_backtrack(const Task* tasks, const int32_t* count, int32_t max_count, const Job* jobs,
+                                  int32_t K, int32_t P, const uint16_t* area16, int32_t* paths, const WsHeader* hdr,
+                                  cudaStream_t st);
 // FV_CHECKED: scan one model's arrays, and the emission scores (dense) or
 // symbols (discrete) of the sequences decoded with it, for values the
 // decoder does not accept; records FV_EINVAL in the header.

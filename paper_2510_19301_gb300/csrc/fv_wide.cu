@@ -351,15 +351,17 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
             j.path_off = jb.path_off;
             j.aux_off = jb.aux_off;
             j.pad = tk.pad;
-            const int qn = a.paths[jb.path_off + tk.n];
-            j.q_n = (unsigned)qn < (unsigned)K ? qn : 0;
-            if (tk.m > 0) {
-              const int qp = a.paths[jb.path_off + tk.m - 1];
-              j.q_prev = (unsigned)qp < (unsigned)K ? qp : 0;
-              j.s_prev = a.sval[jb.aux_off + tk.m - 1];
+            if (!a.ckpt) {
+              const int qn = a.paths[jb.path_off + tk.n];
+              j.q_n = (unsigned)qn < (unsigned)K ? qn : 0;
+              if (tk.m > 0) {
+                const int qp = a.paths[jb.path_off + tk.m - 1];
+                j.q_prev = (unsigned)qp < (unsigned)K ? qp : 0;
+                j.s_prev = a.sval[jb.aux_off + tk.m - 1];
+              }
             }
           }
-          j.Pe = wpe(j.T, a.P);
+          j.Pe = a.ckpt ? ckpt_count(j.T, a.P) : wpe(j.T, a.P);
           L.cur = j;
           L.state = 1;
           L.t = j.m;
@@ -385,15 +387,25 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
         d.q_prev = jb.q_prev;
         d.s_prev = jb.s_prev;
         d.par = jb.par;
-        d.psi_row = kind == kJobLeaf ? (int64_t)(jb.pad + t - jb.m - 1) * K : jb.aux_off + (int64_t)t * K;
+        d.psi_row = kind != kJobLeaf ? jb.aux_off + (int64_t)t * K
+                    : a.ckpt ? 2 * (jb.aux_off + (int64_t)jb.Pe * K) + (int64_t)(t - jb.m - 1) * K
+                             : (int64_t)(jb.pad + t - jb.m - 1) * K;
         if (a.emit == FV_EMIT_DENSE) d.erow = a.E + jb.e_off + (int64_t)t * K;
         else d.sym = __ldg(a.obs + jb.e_off + t);
         if (kind == kJobRoot) {
           const int is_div = (t == L.ediv);
-          if (L.eprev >= 0) d.f_mid = (t == L.eprev + 1) ? 1 : 2;
           d.f_snap = is_div;
-          d.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)L.kdiv * K;
-          d.map_row = (is_div && L.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(L.kdiv - 1) * K : -1;
+          if (a.ckpt) {
+            // checkpoints only: delta_t at division point kdiv
+            d.snap_row = jb.aux_off + (int64_t)L.kdiv * K;
+          } else {
+            if (L.eprev >= 0) d.f_mid = (t == L.eprev + 1) ? 1 : 2;
+            d.snap_row = (int64_t)jb.b * a.snap_stride + (int64_t)L.kdiv * K;
+            d.map_row = (is_div && L.kdiv >= 1) ? (int64_t)jb.b * a.map_stride + (int64_t)(L.kdiv - 1) * K : -1;
+          }
+        } else if (kind == kJobLeaf && a.ckpt && jb.pad >= 0) {
+          // checkpoint segment: the restart reads checkpoint jb.pad
+          d.snap_row = jb.aux_off + (int64_t)jb.pad * K;
         } else if (kind == kJobSub) {
           d.f_mid = (t == L.tmid + 1) ? 1 : (t > L.tmid + 1 ? 2 : 0);
           d.f_snap = (t == L.tmid);
@@ -418,6 +430,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
           ev[u] = a.emit == FV_EMIT_DENSE ? __ldg(d.erow + oj) : __ldg(a.logB + (int64_t)oj * a.V + d.sym);
           if (d.mode == 1) {
             if (d.first) pv[u] = __ldg(a.log_pi + oj);
+            else if (a.ckpt) av[u] = __ldg(a.snaps + d.snap_row + oj);  // checkpoint restart value
             else av[u] = __ldg(a.logA + (int64_t)d.q_prev * K + oj);
           }
         }
@@ -634,6 +647,7 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
       uint32_t mnew = 0;
       if (d.mode == 1) {
         if (d.first) dval = __fadd_rn(pv[u], ev[u]);
+        else if (a.ckpt) dval = av[u];  // delta_m exactly as the forward pass stored it
         else dval = a.complete ? __fadd_rn(av[u], ev[u]) : __fadd_rn(__fadd_rn(d.s_prev, av[u]), ev[u]);
       } else {
         // the lowest rank holding the maximum, then its first chunk reaching
