@@ -13,6 +13,9 @@ share no code.  Every function follows a passage of the paper:
 * ``beam``         -- dynamic beam search of Sec. V-C with per-step beam
                       backpointers (P = 0).
 * ``flash_bs``     -- FLASH-BS (Sec. V-C on top of Alg. 1/Alg. 2).
+* ``beam_static``  -- the static beam the paper contrasts with its dynamic
+                      one (Sec. II-B, Sec. V-C.1): all K scores of a step,
+                      then the top B of them.
 * ``checkpoint``   -- Checkpoint Viterbi, the sqrt(T)-checkpoint baseline of
                       Sec. II-A (forward pass keeping delta at checkpoints,
                       then segments re-decoded latest first).
@@ -82,6 +85,8 @@ def _load():
         lib.orc_path_score.argtypes = [P, i32, P, P]
         lib.orc_path_score.restype = ctypes.c_float
         lib.orc_grad.argtypes = [i32, i32, P, P, P, P, P, P, P, P]
+        lib.orc_beam_static.argtypes = [P, i32, P, i32, P, P]
+        lib.orc_beam_static.restype = ctypes.c_int
         lib.orc_checkpoint.argtypes = [P, i32, P, i32, P, P, P, P]
         lib.orc_checkpoint.restype = ctypes.c_int
         lib.orc_checkpoint_count.argtypes = [i32, i32]
@@ -191,6 +196,19 @@ def beam(hmm: HMM, E, B: int):
     rc = _load().orc_beam(hmm.ref, T, _ptr(E), int(B), _ptr(path), _ptr(score))
     if rc not in (0, 6):
         raise RuntimeError(f"orc_beam failed: {rc}")
+    return path, score[0], rc
+
+
+def beam_static(hmm: HMM, E, B: int):
+    """Static beam (full K-entry score vector per step, then top B) ->
+    (path, score, status); status 6 = empty beam."""
+    E = _E(E, hmm.K)
+    T = E.shape[0]
+    path = np.zeros(T, np.int32)
+    score = np.zeros(1, np.float32)
+    rc = _load().orc_beam_static(hmm.ref, T, _ptr(E), int(B), _ptr(path), _ptr(score))
+    if rc not in (0, 6):
+        raise RuntimeError(f"orc_beam_static failed: {rc}")
     return path, score[0], rc
 
 

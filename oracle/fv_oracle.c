@@ -563,6 +563,94 @@ int orc_beam(const orc_model* m, int32_t T, const float* E, int32_t B,
   return rc;
 }
 
+/* Static beam (the SIEVE-BS style beam the paper contrasts with its own,  */
+/* Sec. II-B and Sec. V-C.1): every step first computes the score of all K */
+/* states -- the best transition from the previous beam, -inf where none   */
+/* leads -- and only then keeps the top B of the whole K-entry vector       */
+/* (score desc, id asc; -inf never kept).  Beam backpointers per step as   */
+/* in orc_beam; the final state is the best entry.                         */
+static const float* g_static_scores;  /* qsort context (single-threaded use per call) */
+static int static_order(const void* a, const void* b) {
+  const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  const float vx = g_static_scores[x], vy = g_static_scores[y];
+  if (vx > vy) return -1;
+  if (vx < vy) return 1;
+  return (x > y) - (x < y);
+}
+static int int_order(const void* a, const void* b) {
+  const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+int orc_beam_static(const orc_model* m, int32_t T, const float* E, int32_t B, int32_t* path, float* score) {
+  if (!m || T < 1 || m->K < 1 || B < 1) return ORC_EINVAL;
+  const int32_t K = m->K, W = B < K ? B : K;
+  float* full = malloc(sizeof(float) * K);      /* scores of all K states, this step */
+  int32_t* from = malloc(sizeof(int32_t) * K);  /* their source state (-1: none)     */
+  int32_t* idx = malloc(sizeof(int32_t) * K);
+  float* bval = malloc(sizeof(float) * W);      /* current beam, id order            */
+  int32_t* bid = malloc(sizeof(int32_t) * W);
+  int32_t* ids = malloc(sizeof(int32_t) * (size_t)T * W);
+  int32_t* src = malloc(sizeof(int32_t) * (size_t)T * W);
+  int32_t* cnt = malloc(sizeof(int32_t) * (size_t)T);
+  if (!full || !from || !idx || !bval || !bid || !ids || !src || !cnt) {
+    free(full); free(from); free(idx); free(bval); free(bid); free(ids); free(src); free(cnt);
+    return ORC_ENOMEM;
+  }
+  int rc = ORC_OK;
+  int32_t nb = 0;
+  for (int32_t t = 0; t < T; ++t) {
+    const float* Et = E + (int64_t)t * K;
+    for (int32_t j = 0; j < K; ++j) { full[j] = -INFINITY; from[j] = -1; }
+    if (t == 0) {
+      for (int32_t j = 0; j < K; ++j) full[j] = m->log_pi[j] + Et[j];
+    } else {
+      for (int32_t j = 0; j < K; ++j) {
+        float best = -INFINITY;
+        int32_t arg = -1;
+        for (int32_t k = 0; k < nb; ++k) {          /* sources in ascending id */
+          const float c = bval[k] + trans(m, bid[k], j);
+          if (arg < 0 || c > best) { best = c; arg = bid[k]; }
+        }
+        if (arg >= 0 && best > -INFINITY) { full[j] = best + Et[j]; from[j] = arg; }
+      }
+    }
+    for (int32_t j = 0; j < K; ++j) idx[j] = j;
+    g_static_scores = full;
+    qsort(idx, (size_t)K, sizeof(int32_t), static_order);
+    int32_t n = 0;
+    while (n < W && n < K && full[idx[n]] > -INFINITY) ++n;
+    qsort(idx, (size_t)n, sizeof(int32_t), int_order);
+    if (n == 0) { rc = ORC_EINFEASIBLE; break; }
+    for (int32_t k = 0; k < n; ++k) {
+      bid[k] = idx[k];
+      bval[k] = full[idx[k]];
+      ids[(int64_t)t * W + k] = idx[k];
+      src[(int64_t)t * W + k] = from[idx[k]];
+    }
+    nb = n;
+    cnt[t] = n;
+  }
+  if (rc == ORC_OK) {
+    int32_t kb = 0;
+    for (int32_t k = 1; k < nb; ++k) if (bval[k] > bval[kb]) kb = k;
+    *score = bval[kb];
+    int32_t q = bid[kb];
+    path[T - 1] = q;
+    for (int32_t t = T - 1; t >= 1; --t) {
+      int32_t k = 0;
+      while (ids[(int64_t)t * W + k] != q) ++k;
+      q = src[(int64_t)t * W + k];
+      path[t - 1] = q;
+    }
+  } else {
+    for (int32_t t = 0; t < T; ++t) path[t] = 0;
+    *score = -INFINITY;
+  }
+  free(full); free(from); free(idx); free(bval); free(bid); free(ids); free(src); free(cnt);
+  return rc;
+}
+
 /* Index of state `id` in an id-sorted beam (binary search); -1 if absent. */
 static int32_t beam_find(const orc_cand* beam, int32_t nb, int32_t id) {
   int32_t lo = 0, hi = nb - 1;

@@ -183,3 +183,42 @@ def test_csr_beam_matches_restatement_on_dense_equivalent(case, B):
         assert rc == 6
         return
     assert rc == 0 and np.array_equal(p, ref[0]) and bits(s) == bits(ref[1])
+
+
+@settings(max_examples=150, deadline=None)
+@given(model_strategy(max_k=6, max_t=7), st.integers(1, 7))
+def test_static_beam_matches_restatement_and_dynamic(case, B):
+    """The static beam (all K scores of a step, then the top B) against the
+    Python restatement of the beam (which sorts every candidate) and the
+    oracle's dynamic beam: same paths and score bits, same infeasibility.
+    With B >= K it is exact decoding."""
+    lp, A, E = case
+    K = lp.shape[0]
+    hmm = oracle.HMM(lp, A)
+    Bc = min(B, K)
+    ref = beam_restated(lp, A, E, Bc)
+    p, s, rc = oracle.beam_static(hmm, E, B)
+    pd, sd, rcd = oracle.beam(hmm, E, B)
+    assert rc == rcd
+    if ref is None:
+        assert rc == 6
+        return
+    assert rc == 0 and np.array_equal(p, ref[0]) and bits(s) == bits(ref[1])
+    assert np.array_equal(p, pd) and bits(s) == bits(sd)
+    if B >= K:
+        pv, sv = oracle.viterbi(hmm, E)
+        assert np.array_equal(p, pv) and bits(s) == bits(sv)
+
+
+@settings(max_examples=80, deadline=None)
+@given(csr_case(), st.integers(1, 6))
+def test_static_beam_csr_matches_restatement(case, B):
+    lp, E, rp, col, val, dense = case
+    K = lp.shape[0]
+    csr = oracle.HMM(lp, row_ptr=rp, col=col, val=val)
+    ref = beam_restated(lp, dense, E, min(B, K))
+    p, s, rc = oracle.beam_static(csr, E, B)
+    if ref is None:
+        assert rc == 6
+        return
+    assert rc == 0 and np.array_equal(p, ref[0]) and bits(s) == bits(ref[1])
