@@ -569,17 +569,16 @@ int orc_beam(const orc_model* m, int32_t T, const float* E, int32_t B,
 /* leads -- and only then keeps the top B of the whole K-entry vector       */
 /* (score desc, id asc; -inf never kept).  Beam backpointers per step as   */
 /* in orc_beam; the final state is the best entry.                         */
-static const float* g_static_scores;  /* qsort context (single-threaded use per call) */
-static int static_order(const void* a, const void* b) {
-  const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
-  const float vx = g_static_scores[x], vy = g_static_scores[y];
-  if (vx > vy) return -1;
-  if (vx < vy) return 1;
-  return (x > y) - (x < y);
+typedef struct { float v; int32_t id; } orc_entry;
+static int entry_order(const void* a, const void* b) {  /* score desc, id asc */
+  const orc_entry* x = a; const orc_entry* y = b;
+  if (x->v > y->v) return -1;
+  if (x->v < y->v) return 1;
+  return (x->id > y->id) - (x->id < y->id);
 }
-static int int_order(const void* a, const void* b) {
-  const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
-  return (x > y) - (x < y);
+static int entry_id_order(const void* a, const void* b) {
+  const orc_entry* x = a; const orc_entry* y = b;
+  return (x->id > y->id) - (x->id < y->id);
 }
 
 int orc_beam_static(const orc_model* m, int32_t T, const float* E, int32_t B, int32_t* path, float* score) {
@@ -587,7 +586,7 @@ int orc_beam_static(const orc_model* m, int32_t T, const float* E, int32_t B, in
   const int32_t K = m->K, W = B < K ? B : K;
   float* full = malloc(sizeof(float) * K);      /* scores of all K states, this step */
   int32_t* from = malloc(sizeof(int32_t) * K);  /* their source state (-1: none)     */
-  int32_t* idx = malloc(sizeof(int32_t) * K);
+  orc_entry* idx = malloc(sizeof(orc_entry) * K);
   float* bval = malloc(sizeof(float) * W);      /* current beam, id order            */
   int32_t* bid = malloc(sizeof(int32_t) * W);
   int32_t* ids = malloc(sizeof(int32_t) * (size_t)T * W);
@@ -615,18 +614,18 @@ int orc_beam_static(const orc_model* m, int32_t T, const float* E, int32_t B, in
         if (arg >= 0 && best > -INFINITY) { full[j] = best + Et[j]; from[j] = arg; }
       }
     }
-    for (int32_t j = 0; j < K; ++j) idx[j] = j;
-    g_static_scores = full;
-    qsort(idx, (size_t)K, sizeof(int32_t), static_order);
+    for (int32_t j = 0; j < K; ++j) { idx[j].v = full[j]; idx[j].id = j; }
+    qsort(idx, (size_t)K, sizeof(orc_entry), entry_order);
     int32_t n = 0;
-    while (n < W && n < K && full[idx[n]] > -INFINITY) ++n;
-    qsort(idx, (size_t)n, sizeof(int32_t), int_order);
+    while (n < W && n < K && idx[n].v > -INFINITY) ++n;
+    qsort(idx, (size_t)n, sizeof(orc_entry), entry_id_order);
     if (n == 0) { rc = ORC_EINFEASIBLE; break; }
     for (int32_t k = 0; k < n; ++k) {
-      bid[k] = idx[k];
-      bval[k] = full[idx[k]];
-      ids[(int64_t)t * W + k] = idx[k];
-      src[(int64_t)t * W + k] = from[idx[k]];
+      const int32_t j = idx[k].id;
+      bid[k] = j;
+      bval[k] = full[j];
+      ids[(int64_t)t * W + k] = j;
+      src[(int64_t)t * W + k] = from[j];
     }
     nb = n;
     cnt[t] = n;
