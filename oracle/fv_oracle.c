@@ -604,14 +604,20 @@ int orc_beam_static(const orc_model* m, int32_t T, const float* E, int32_t B, in
     if (t == 0) {
       for (int32_t j = 0; j < K; ++j) full[j] = m->log_pi[j] + Et[j];
     } else {
-      for (int32_t j = 0; j < K; ++j) {
-        float best = -INFINITY;
-        int32_t arg = -1;
-        for (int32_t k = 0; k < nb; ++k) {          /* sources in ascending id */
-          const float c = bval[k] + trans(m, bid[k], j);
-          if (arg < 0 || c > best) { best = c; arg = bid[k]; }
+      /* each state's best transition from the beam: sources visited in */
+      /* ascending id, so a target keeps its first strict maximum         */
+      for (int32_t k = 0; k < nb; ++k) {
+        const int32_t i = bid[k];
+        const int32_t e0 = m->csr ? m->row_ptr[i] : 0, e1 = m->csr ? m->row_ptr[i + 1] : K;
+        for (int32_t e = e0; e < e1; ++e) {
+          const int32_t j = m->csr ? m->col[e] : e;
+          const float c = bval[k] + (m->csr ? m->val[e] : m->logA[(int64_t)i * K + j]);
+          if (from[j] < 0 || c > full[j]) { full[j] = c; from[j] = i; }
         }
-        if (arg >= 0 && best > -INFINITY) { full[j] = best + Et[j]; from[j] = arg; }
+      }
+      for (int32_t j = 0; j < K; ++j) {
+        if (from[j] >= 0 && full[j] > -INFINITY) full[j] = full[j] + Et[j];
+        else { full[j] = -INFINITY; from[j] = -1; }
       }
     }
     for (int32_t j = 0; j < K; ++j) { idx[j].v = full[j]; idx[j].id = j; }
