@@ -512,6 +512,50 @@ def config3_sparse(fv, T, device, lib):
     return out
 
 
+def static_vs_dynamic_beam(fv, device, lib):
+    """The static beam the paper contrasts with its dynamic one (Sec. II-B,
+    Sec. V-C.1) against the dynamic beam, same inputs, same results: time per
+    decode and the candidate storage each step needs (static: the score and
+    source of all K states, in the workspace; dynamic: only the states the
+    beam reaches, listed in shared memory for CSR)."""
+    import torch
+
+    import workloads as W
+    rows = {}
+    cases = []
+    rng = np.random.default_rng(77)
+    log_pi, logA = W.random_model(1024, rng)
+    md = fv.Model(log_pi, logA, device=device)
+    Ed = torch.from_numpy(W.gaussian_emissions(64 * 2000, 1024, rng)).to(device)
+    cases.append(("dense_K1024_B256_64x2000", md, fv.Batch([2000] * 64, E=Ed.view(-1), models=[md], device=device),
+                  256, 1024))
+    log_pi, rp, col, val = W.config3_sparse_model()
+    ms = fv.Model(log_pi, row_ptr=rp, col=col, val=val, device=device)
+    Es = W.gaussian_emissions_packed_device(8 * 500, 65536, seed=4, device=device, chunk_rows=1 << 13)
+    bs = fv.Batch([500] * 8, E=Es.view(-1), models=[ms], device=device)
+    for B in (128, 512, 2048):
+        cases.append((f"csr_K65536_B{B}_8x500", ms, bs, B, 65536))
+    for name, m, b, B, K in cases:
+        row = {}
+        res = {}
+        for kind, flags in (("dynamic", 0), ("static", fv._lib.FV_STATIC_BEAM)):
+            d = fv.Decoder([m], b, mode="beam", B=B, P=0, flags=flags)
+            d(check=True)
+            ms_, _ = time_decoder(d, 3, 1, lib)
+            res[kind] = (d.paths.clone(), d.scores.clone())
+            row[kind] = {"ms": ms_, "workspace_bytes": d.ws_bytes}
+            del d
+        row["static"]["candidate_bytes_per_step"] = 8 * K
+        row["dynamic"]["candidate_bytes_per_step"] = 8 * (min(K, 32 * B) if K == 65536 else K)
+        row["static_over_dynamic_time"] = row["static"]["ms"] / row["dynamic"]["ms"]
+        row["identical"] = bool(torch.equal(res["static"][0], res["dynamic"][0]) and torch.equal(
+            res["static"][1].view(torch.int32), res["dynamic"][1].view(torch.int32)))
+        rows[name] = row
+    del Ed, Es
+    torch.cuda.empty_cache()
+    return rows
+
+
 def serving_run(seconds, rate=2000.0, n_streams=128, max_wall=30.0):
     """Serving loop: Poisson arrivals, mixed K and T, exact and beam B=256,
     admitted under a 40 GB device-memory budget.  Admission stops after
@@ -762,6 +806,8 @@ def run_ours(args):
         out["config3_dense"] = config3_dense(fv, args.c3_T, device, lib)
     if rank == 0 and args.c3s_T > 0:
         out["config3_sparse"] = config3_sparse(fv, args.c3s_T, device, lib)
+    if rank == 0 and not args.quick:
+        out["beam_static_vs_dynamic"] = static_vs_dynamic_beam(fv, device, lib)
     if rank == 0 and args.serve_seconds > 0:
         out["serving"] = serving_run(args.serve_seconds)
         # the same request mix at a rate below the measured capacity: the

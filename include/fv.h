@@ -77,6 +77,14 @@ typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
 /* Run the default engine configuration instead of the one chosen by
  * fv_autotune / fv_set_engine_variant. */
 #define FV_NO_TUNE 0x8u
+/* FV_BEAM: run the static beam the paper contrasts with its dynamic one
+ * (Sec. II-B; Sec. V-C.1), as in SIEVE-BS: every step first writes the
+ * score of all K states (-inf where no beam state leads) to the workspace,
+ * then keeps the top B of those K entries.  Same beams, paths and scores as
+ * the dynamic beam (the top-B rule is the same); only the work per step and
+ * the per-step candidate storage differ (K entries instead of the states
+ * the beam reaches).  A comparator for benchmarks. */
+#define FV_STATIC_BEAM 0x10u
 /* Test hook for failure detection: the first CTA of the whole-GPU engine
  * (dense K > 1024) never publishes its step count, and CTA 1 of every 4- or
  * 8-CTA cluster of the streamed engine (256 < K <= 1024) withholds its

@@ -24,6 +24,7 @@ FV_COMPLETE_PRUNING = 0x1
 FV_NO_SORT = 0x2
 FV_CHECKED = 0x4
 FV_NO_TUNE = 0x8
+FV_STATIC_BEAM = 0x10
 FV_TEST_WITHHOLD_STEP = 0x80000000
 
 P = ctypes.c_void_p

@@ -404,6 +404,22 @@ __device__ inline void clear_candidates(const BeamArgs& a, BeamScratch& S, BeamS
   __syncthreads();
 }
 
+// Static beam: the step's full K-entry score vector -- -inf (and no
+// source) for every state no beam state leads to -- and every state marked
+// as an entry, so the top-B select reads all K scores.
+__device__ inline void static_full_vector(const BeamArgs& a, BeamScratch& S, BeamSmem& sm) {
+  sm.nlist = -1;
+  for (int j = threadIdx.x; j < a.K; j += blockDim.x)
+    if (!((sm.touched[j >> 5] >> (j & 31)) & 1u)) {
+      S.cval[j] = -CUDART_INF_F;
+      S.cslot[j] = -1;
+    }
+  __syncthreads();
+  for (int w = threadIdx.x; w < ((a.K + 31) >> 5); w += blockDim.x)
+    sm.touched[w] = (w == (a.K >> 5)) ? ((1u << (a.K & 31)) - 1u) : 0xffffffffu;
+  __syncthreads();
+}
+
 // Candidates of step t from beam buffer p (size nb) into cval/cslot/touched.
 __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const Job& jb, int p, int nb, int t) {
   const int K = a.K;
@@ -468,6 +484,7 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
       }
     }
     __syncthreads();
+    if (a.static_beam) static_full_vector(a, S, sm);
     return;
   }
   if (a.trans == FV_TRANS_DENSE) {
@@ -510,6 +527,7 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
       }
     }
     __syncthreads();
+    if (a.static_beam) static_full_vector(a, S, sm);
     return;
   }
   // CSR: warp per beam entry scatters keys
@@ -565,6 +583,7 @@ __device__ void beam_candidates(const BeamArgs& a, BeamScratch& S, BeamSmem& sm,
       if ((sm.touched[j >> 5] >> (j & 31)) & 1u) cand(j);
   }
   __syncthreads();
+  if (a.static_beam) static_full_vector(a, S, sm);
 }
 
 // Initial candidates at t = m: from pi (m = 0) or from the single state
@@ -601,6 +620,7 @@ __device__ void beam_init(const BeamArgs& a, BeamScratch& S, BeamSmem& sm, const
     }
   }
   __syncthreads();
+  if (a.static_beam) static_full_vector(a, S, sm);
 }
 
 // Block-wide (max value, lowest index) over per-thread candidates; idx
@@ -864,7 +884,8 @@ cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   const size_t cand_bytes = sizeof(int32_t) * 2 * (size_t)a.K;
   b.beam_smem = smem + beam_bytes <= (size_t)160 * 1024;
   if (b.beam_smem) smem += beam_bytes;
-  b.cand_smem = smem + cand_bytes <= (size_t)208 * 1024;
+  // the static beam keeps its full score vector in the workspace
+  b.cand_smem = !a.static_beam && smem + cand_bytes <= (size_t)208 * 1024;
   if (b.cand_smem) smem += cand_bytes;
   // CSR with candidates in global memory: a shared-memory list of each
   // step's touched candidates (8 bytes each) for the top-B select
@@ -872,7 +893,7 @@ cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   // step with more touched candidates uses the K-indexed arrays.  Not used
   // when it would take most of the L1 cache the CSR gathers rely on.
   b.list_cap = 0;
-  if (!b.cand_smem && a.trans != FV_TRANS_DENSE) {
+  if (!b.cand_smem && !a.static_beam && a.trans != FV_TRANS_DENSE) {
     size_t cap = (size_t)a.Bcap * 32;
     if (cap > (size_t)a.K) cap = (size_t)a.K;
     cap = (cap + 3) & ~(size_t)3;  // keeps the id array 16-byte aligned

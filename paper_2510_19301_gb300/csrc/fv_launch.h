@@ -172,6 +172,10 @@ struct BeamArgs {
   int32_t cand_smem;          // candidate values / sources live in shared memory
   int32_t list_cap;           // CSR with candidates in global memory: entries of the shared-memory
                               // list of a step's touched candidates (ordered key, state id); 0 = none
+  // static beam (the SIEVE-BS style comparator of Sec. II-B / V-C.1): every
+  // step writes the full K-entry score vector (-inf where no beam state
+  // leads) to the workspace and selects the top B from all K entries
+  int32_t static_beam;
   WsHeader* hdr;
 };
 
