@@ -1,22 +1,35 @@
 """Continuous-batching decode server (not in the paper).
 
-Requests (an HMM, emission scores, a mode) arrive over time.  The server
-keeps a FIFO of waiting requests and a set of in-flight ones.  Each loop
-iteration it
+Requests (an observation sequence to decode with an HMM of one of the
+served state-space sizes, a mode) arrive over time.  The server keeps a FIFO
+of waiting requests and a set of in-flight launches.  Each loop iteration it
 
-  1. reaps finished requests (event polling; latency = completion - arrival),
+  1. reaps finished launches (event polling; a request's latency is the
+     completion of its launch minus its arrival),
   2. admits waiting requests in arrival order while the device-memory budget
-     (decoder workspace + inputs + outputs of every in-flight request) and
-     the stream slots allow,
-  3. launches every admitted request's decode on its own stream, so requests
-     that arrive while others are on the GPU overlap with them.
+     (workspace + inputs + outputs of everything in flight) and the launch
+     slots allow,
+  3. packs the admitted requests of one class -- same K, same mode and beam
+     parameters -- into ONE ``fv_decode`` batch and launches it on a free
+     stream.  Inside the launch the persistent engine refills its sequence
+     slots at tick granularity, so the requests of a batch share clusters
+     and logA tiles; launches of different classes and of later arrivals
+     run concurrently on other streams and SMs.
 
-Device state (delta/backpointers in the workspace) stays on the device for
-the whole life of a request.  The decode itself is one ``fv_decode`` call
-per request; nothing is computed on the host.
+Device state (delta / backpointers in the workspace) stays on the device for
+the whole life of a launch; nothing is computed on the host.
+
+Models: by default the server holds one model per K class (Dirichlet(1)
+transitions and initial distribution, drawn once from a fixed seed) and
+every request brings its own emission scores, drawn on the device from the
+request's seed; requests of one class can then share engine slots.  With
+``shared_models=False`` every request also brings its own model; a batch
+then carries one model per request (at most 64 per launch, the engine's
+model table) and the engine decodes them model by model.
 
 The backend is pluggable: ``GpuBackend`` runs libfv; tests drive the
-admission and failure logic with a host-only fake.
+admission, batching and failure logic with host-only fakes.  A backend
+without ``launch_batch`` is driven one request per launch.
 """
 from __future__ import annotations
 
@@ -50,21 +63,29 @@ class Request:
     def latency(self):
         return self.finished - self.arrival
 
+    @property
+    def klass(self):
+        """Requests of one class can share one launch."""
+        return (self.K, self.mode, self.B if self.mode == "beam" else 0, self.P if self.mode != "exact" else 0)
+
 
 class Server:
     def __init__(self, backend, mem_budget_bytes: int = 40 << 30, max_inflight: int = 64,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, max_batch: int = 1024):
         self.backend = backend
         self.budget = int(mem_budget_bytes)
-        self.max_inflight = int(max_inflight)
+        self.max_inflight = int(max_inflight)   # launches in flight
+        self.max_batch = int(max_batch)         # requests per launch
         self.clock = clock
+        self.batched = hasattr(backend, "launch_batch")
         self.waiting: collections.deque[Request] = collections.deque()
-        self.inflight: list[tuple[Request, object]] = []
+        self.inflight: list[tuple[list[Request], object]] = []
         self.done: list[Request] = []
         self.failed: list[Request] = []
         self.bytes_in_use = 0
         self.peak_bytes = 0
         self.not_served = 0
+        self.launches = 0
         self.t0 = None
 
     def now(self):
@@ -73,46 +94,72 @@ class Server:
     def submit(self, req: Request):
         self.waiting.append(req)
 
-    def step(self):
-        # 1. reap
+    def _reap(self):
         still = []
-        for req, handle in self.inflight:
+        for reqs, handle in self.inflight:
             st = self.backend.poll(handle)
             if st is None:
-                still.append((req, handle))
+                still.append((reqs, handle))
                 continue
-            req.finished = self.now()
-            req.status = st
-            req.result = self.backend.result(handle)
+            t = self.now()
+            sts = st if isinstance(st, (list, tuple)) else [st] * len(reqs)
+            for i, req in enumerate(reqs):
+                req.finished = t
+                req.status = int(sts[i])
+                req.result = self.backend.result(handle, i) if self.batched else self.backend.result(handle)
+                self.bytes_in_use -= req.nbytes
+                (self.done if req.status == 0 else self.failed).append(req)
             self.backend.release(handle)
-            self.bytes_in_use -= req.nbytes
-            (self.done if st == 0 else self.failed).append(req)
         self.inflight = still
-        # 2./3. admit in arrival order while memory and slots allow
-        while self.waiting and len(self.inflight) < self.max_inflight:
+
+    def _fail(self, req, status):
+        req.status = status
+        req.finished = self.now()
+        self.failed.append(req)
+
+    def step(self):
+        self._reap()
+        # admit in arrival order while memory allows; group by class
+        groups: dict[tuple, list[Request]] = {}
+        order: list[tuple] = []
+        n_launch = len(self.inflight)
+        while self.waiting:
             req = self.waiting[0]
             need = self.backend.bytes_needed(req)
             if need > self.budget:  # can never fit: reject instead of blocking the queue
                 self.waiting.popleft()
-                req.status = -2
-                req.finished = self.now()
-                self.failed.append(req)
+                self._fail(req, -2)
                 continue
             if self.bytes_in_use + need > self.budget:
                 break
+            key = req.klass if self.batched else ("req", req.rid)
+            if key not in groups:
+                if n_launch >= self.max_inflight:
+                    break
+                groups[key] = []
+                order.append(key)
+                n_launch += 1
+            elif len(groups[key]) >= self.max_batch:
+                break
             self.waiting.popleft()
-            try:
-                handle = self.backend.launch(req)
-            except Exception:  # launch failure is reported, not retried
-                req.status = -3
-                req.finished = self.now()
-                self.failed.append(req)
-                continue
-            req.admitted = self.now()
             req.nbytes = need
             self.bytes_in_use += need
-            self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
-            self.inflight.append((req, handle))
+            groups[key].append(req)
+        self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
+        for key in order:
+            reqs = groups[key]
+            try:
+                handle = self.backend.launch_batch(reqs) if self.batched else self.backend.launch(reqs[0])
+            except Exception:  # launch failure is reported, not retried
+                for req in reqs:
+                    self.bytes_in_use -= req.nbytes
+                    self._fail(req, -3)
+                continue
+            t = self.now()
+            for req in reqs:
+                req.admitted = t
+            self.launches += 1
+            self.inflight.append((reqs, handle))
 
     def run(self, requests, realtime: bool = True, idle_sleep: float = 0.0, max_wall: float = math.inf):
         """Replay requests at their arrival times (host clock) until all are
@@ -128,7 +175,7 @@ class Server:
                 self.waiting.clear()
                 i = len(reqs)
                 while self.inflight:
-                    self.step()
+                    self._reap()
                 break
             now = self.now()
             while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
@@ -153,15 +200,22 @@ class Server:
             "state_steps_per_s": steps / wall if wall else None,
             "cells_per_s": cells / wall if wall else None,
             "wall_s": wall, "peak_bytes": self.peak_bytes, "budget_bytes": self.budget,
+            "launches": self.launches,
+            "requests_per_launch": len(self.done + self.failed) / self.launches if self.launches else None,
         }
 
 
 class GpuBackend:
-    """libfv backend: one stream per in-flight request from a pool; model and
-    emission scores are drawn on that stream (seeded by the request) before
-    the decode, so the host never touches them."""
+    """libfv backend: one stream per in-flight launch from a pool.  A launch
+    decodes a batch of requests of one class with one ``fv_decode`` call;
+    each request's emission scores are drawn on that stream from its seed
+    (and, without shared models, its model too), so the host never touches
+    them."""
 
-    def __init__(self, n_streams: int = 32, device: str = "cuda", keep_results: bool = False):
+    MAX_MODELS = 64  # the engine's model table per launch
+
+    def __init__(self, n_streams: int = 32, device: str = "cuda", keep_results: bool = False,
+                 shared_models: bool = True, model_seed: int = 6):
         import torch
 
         from . import Batch, Decoder, Model
@@ -171,47 +225,69 @@ class GpuBackend:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
         self.free = list(range(n_streams))
         self.keep = keep_results
+        self.shared = shared_models
+        self.model_seed = int(model_seed)
+        self._models = {}
 
     # -- inputs -----------------------------------------------------------
-    def make_inputs(self, req: Request):
-        """Dirichlet(1) model and log_softmax(N(0,1)) emissions, seeded."""
+    def _dirichlet_model(self, K, seed):
+        torch = self.torch
+        g = torch.Generator(device=self.device)
+        g.manual_seed(int(seed))
+        gam = torch._standard_gamma(torch.ones((K + 1, K), device=self.device, dtype=torch.float64), generator=g)
+        probs = gam / gam.sum(dim=1, keepdim=True)
+        return probs[K].log().float(), probs[:K].log().float()
+
+    def model_for(self, K):
+        """The served model of class K (shared models): Dirichlet(1) rows and
+        initial distribution from a fixed seed, drawn once."""
+        if K not in self._models:
+            self._models[K] = self._dirichlet_model(K, self.model_seed * 100003 + K)
+        return self._models[K]
+
+    def emissions(self, req: Request, out=None):
+        """log_softmax(N(0,1)) emission scores of the request, from its seed
+        (after its model's draws when it brings its own model)."""
         torch = self.torch
         g = torch.Generator(device=self.device)
         g.manual_seed(int(req.seed))
-        K = req.K
-        gam = torch._standard_gamma(torch.ones((K + 1, K), device=self.device, dtype=torch.float64), generator=g)
-        probs = gam / gam.sum(dim=1, keepdim=True)
-        log_pi = probs[K].log().float()
-        logA = probs[:K].log().float()
-        x = torch.randn((req.T, K), generator=g, device=self.device, dtype=torch.float32)
+        if not self.shared:
+            torch._standard_gamma(torch.ones((req.K + 1, req.K), device=self.device, dtype=torch.float64),
+                                  generator=g)
+        x = torch.randn((req.T, req.K), generator=g, device=self.device, dtype=torch.float32)
         E = torch.log_softmax(x.double(), dim=-1).float()
-        return log_pi, logA, E
+        if out is not None:
+            out.copy_(E.view(-1))
+            return out
+        return E
 
-    def _decoder(self, req, log_pi, logA, E):
-        m = self.Model(log_pi, logA, device=self.device)
-        b = self.Batch([req.T], E=E.view(-1), models=[m], device=self.device)
-        mode = {"exact": "vanilla", "flash": "flash", "beam": "beam"}[req.mode]
-        return self.Decoder([m], b, mode=mode, P=req.P if req.mode != "exact" else 1,
-                            B=req.B if req.mode == "beam" else 0)
+    def make_inputs(self, req: Request):
+        """(log_pi, logA, E) of a request, exactly as a launch draws them."""
+        if self.shared:
+            log_pi, logA = self.model_for(req.K)
+        else:
+            log_pi, logA = self._dirichlet_model(req.K, req.seed)
+        return log_pi, logA, self.emissions(req)
 
-    def tune(self, Ks=(64, 256, 1024), T=2000):
-        """Engine configuration of each K class picked by the autotuner on one
-        representative request (a single sequence of T steps): requests here
-        are single sequences, not the full batches the defaults were chosen
-        for.  Results do not depend on the choice.  Returns {K: variant}."""
+    @staticmethod
+    def _mode(req):
+        return {"exact": "vanilla", "flash": "flash", "beam": "beam"}[req.mode]
+
+    def tune(self, Ks=(64, 256, 1024), T=2000, n=16):
+        """Engine configuration of each K class picked by the autotuner on a
+        representative launch (n requests of T steps).  Results do not depend
+        on the choice.  Returns {K: variant}."""
         from . import autotune
         chosen = {}
         for K in Ks:
-            req = Request(rid=-1, K=int(K), T=int(T), seed=12345 + int(K))
-            log_pi, logA, E = self.make_inputs(req)
-            m = self.Model(log_pi, logA, device=self.device)
-            b = self.Batch([req.T], E=E.view(-1), models=[m], device=self.device)
-            chosen[int(K)] = int(autotune([m], b, mode="vanilla")[0])
+            reqs = [Request(rid=-1 - i, K=int(K), T=int(T), seed=12345 + int(K) + i) for i in range(n)]
+            dec, _, _ = self._batch_decoder(reqs)
+            chosen[int(K)] = int(autotune(dec.models, dec.batch, mode="vanilla")[0])
         return chosen
 
     def bytes_needed(self, req: Request):
         K, T = req.K, req.T
-        inputs = 4 * (K * K + K + T * K)
+        inputs = 4 * (T * K) + (0 if self.shared else 4 * (K * K + K))
         outputs = 4 * (T + 1)
         if req.mode == "exact":
             ws = 2 * T * K
@@ -226,31 +302,63 @@ class GpuBackend:
             return (req.T - 1) * min(req.B, req.K) * req.K
         return (req.T - 1) * req.K * req.K
 
-    def launch(self, req: Request):
+    def _batch_decoder(self, reqs):
+        """Inputs and a prepared decoder for one class of requests."""
+        torch = self.torch
+        r0 = reqs[0]
+        K = r0.K
+        lengths = [r.T for r in reqs]
+        E = torch.empty(sum(lengths) * K, dtype=torch.float32, device=self.device)
+        off = 0
+        for r in reqs:
+            self.emissions(r, out=E[off:off + r.T * K])
+            off += r.T * K
+        if self.shared:
+            log_pi, logA = self.model_for(K)
+            models = [self.Model(log_pi, logA, device=self.device)]
+            mi = None
+        else:
+            models = [self.Model(*self._dirichlet_model(K, r.seed), device=self.device) for r in reqs]
+            mi = list(range(len(reqs)))
+        b = self.Batch(lengths, E=E, models=models, model_index=mi, device=self.device)
+        dec = self.Decoder(models, b, mode=self._mode(r0), P=r0.P if r0.mode != "exact" else 1,
+                           B=r0.B if r0.mode == "beam" else 0)
+        return dec, E, models
+
+    def launch_batch(self, reqs):
         torch = self.torch
         if not self.free:
             raise RuntimeError("no free stream")
+        if not self.shared and len(reqs) > self.MAX_MODELS:
+            raise ValueError("a launch carries at most 64 models")
         si = self.free.pop()
         st = self.streams[si]
-        with torch.cuda.stream(st):
-            log_pi, logA, E = self.make_inputs(req)
-            dec = self._decoder(req, log_pi, logA, E)
-            dec.launch(st)
-            ev = torch.cuda.Event()
-            ev.record(st)
-        return {"si": si, "dec": dec, "ev": ev, "inputs": (log_pi, logA, E)}
+        try:
+            with torch.cuda.stream(st):
+                dec, E, models = self._batch_decoder(reqs)
+                dec.launch(st)
+                ev = torch.cuda.Event()
+                ev.record(st)
+        except Exception:
+            self.free.append(si)
+            raise
+        return {"si": si, "dec": dec, "ev": ev, "inputs": (E, models), "n": len(reqs)}
+
+    def launch(self, req: Request):
+        return self.launch_batch([req])
 
     def poll(self, h):
         if not h["ev"].query():
             return None
         return h["dec"].device_status(self.streams[h["si"]])
 
-    def result(self, h):
+    def result(self, h, i=0):
         if not self.keep:
             return None
         d = h["dec"]
-        T = d.batch.path_len
-        return d.paths[:T].cpu().numpy(), float(d.scores[0].item())
+        off = int(d.batch.path_off_host[i])
+        T = int(d.batch.T_host[i])
+        return d.paths[off:off + T].cpu().numpy(), float(d.scores[i].item())
 
     def release(self, h):
         self.free.append(h["si"])

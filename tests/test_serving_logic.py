@@ -83,3 +83,49 @@ def test_inflight_limit_and_latency_stats():
     lat = sorted(r.latency for r in srv.done)
     assert rep["p50_ms"] == pytest.approx(1e3 * (lat[4] + lat[5]) / 2)
     assert all(r.admitted >= r.arrival for r in srv.done)
+
+
+class FakeBatchBackend(FakeBackend):
+    """Backend that takes one launch per class of requests."""
+
+    def __init__(self, work_ticks=3, fail_rids=()):
+        super().__init__(work_ticks, fail_rids)
+        self.batches = []
+
+    def launch_batch(self, rs):
+        if any(r.rid in self.fail for r in rs):
+            raise RuntimeError("injected launch failure")
+        self.batches.append([r.rid for r in rs])
+        return {"left": self.work, "n": len(rs)}
+
+    def result(self, h, i=0):
+        return None
+
+
+def test_batched_launches_group_one_class_and_keep_fifo():
+    be = FakeBatchBackend(work_ticks=4)
+    rs = [Request(rid=i, K=(64 if i % 3 else 256), T=10, mode=("beam" if i % 2 else "exact"), arrival=0.0)
+          for i in range(12)]
+    srv = Server(be, mem_budget_bytes=10**9, max_inflight=16, clock=FakeClock())
+    rep = srv.run(rs, realtime=False)
+    assert rep["requests"] == 12 and rep["failed"] == 0
+    # every launch holds requests of one class, in arrival order
+    for b in be.batches:
+        assert len({rs[i].klass for i in b}) == 1 and b == sorted(b)
+    assert len(be.batches) == len({r.klass for r in rs})
+    assert rep["launches"] == len(be.batches) and rep["requests_per_launch"] == 12 / len(be.batches)
+    # a request finishes with its launch
+    for b in be.batches:
+        assert len({srv.done[[r.rid for r in srv.done].index(i)].finished for i in b}) == 1
+
+
+def test_batched_budget_and_failures():
+    be = FakeBatchBackend(fail_rids={5})
+    rs = [Request(rid=i, K=30 + (i % 2), T=10, arrival=0.001 * i) for i in range(10)]
+    srv = Server(be, mem_budget_bytes=100, max_inflight=8, clock=FakeClock(), max_batch=2)
+    rep = srv.run(rs, realtime=False)
+    assert srv.peak_bytes <= 100 and srv.bytes_in_use == 0
+    assert all(len(b) <= 2 for b in be.batches)
+    failed = sorted(r.rid for r in srv.failed)
+    assert 5 in failed and rep["requests"] + rep["failed"] == 10
+    assert all(r.status == -3 for r in srv.failed)
