@@ -440,7 +440,52 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   int cur = 0;
   int tick = 0;
   for (;; ++tick) {
-    // ---- prologue: slot state machine (identical in every CTA)
+    int tick_live = 0;
+
+    // ---- streamed: the first ring stages of this tick's logA rows
+    const int sg = lane / LJ, jg = lane % LJ;
+    const int cg = warp % CG, rg = warp / CG;
+    float2* ring = STREAM ? reinterpret_cast<float2*>(sA) + warp * NST * 2 * WC : nullptr;
+    const float2* gsrc = STREAM ? a.Ap + (int64_t)(rg * C / 2) * a.ap_stride + j0 + cg * WC : nullptr;
+    constexpr int NIT = C / 4;
+    auto issue = [&](int it) {
+      float2* dst = ring + (it % NST) * 2 * WC;
+#pragma unroll
+      for (int u = 0; u < WC / 32; ++u) {
+        const int q = lane + 32 * u, pr = q / (WC / 2), c2 = (q % (WC / 2)) * 2;
+        cp_async16(dst + pr * WC + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
+      }
+    };
+    if constexpr (STREAM) {
+#pragma unroll
+      for (int k = 0; k < NST - 1; ++k) {
+        if (k < NIT) issue(k);
+        cp_async_commit();
+      }
+    }
+
+    // ---- multi-CTA clusters: wait until delta_{t-1} of every CTA is here
+    if constexpr (CL > 1 && kExch != 0) {
+      if (tick > 0) {
+        const uint32_t bar = smem_addr(&s_bar[(tick - 1) & 1]);
+        const uint32_t par = (uint32_t)((tick - 1) >> 1) & 1u;
+        if (!mbar_try_wait_cluster(bar, par)) {
+          const long long w0 = clock64();
+          while (!mbar_try_wait_cluster(bar, par)) {
+            if (clock64() - w0 > kClusterWaitCycles) {
+              set_status(a.hdr, FV_ETIMEOUT, 3);
+              s_abort = 1;
+              break;
+            }
+          }
+        }
+      }
+    }
+
+    // ---- prologue: slot state machine (identical in every CTA), run by
+    // the slots' owner threads in warp 0 while the other warps start this
+    // tick's max-plus loop, which does not depend on it; the barrier after
+    // the loop publishes the descriptors
     {
       TickDesc td;
       td.mode = 0;
@@ -584,119 +629,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           s_info[tick & 1][4] = trm;
         }
       }
-      if (!__syncthreads_or(live)) break;
-    }
-    const uint32_t m_act = s_info[tick & 1][0], m_mid = s_info[tick & 1][1], m_snp = s_info[tick & 1][2];
-    const uint32_t m_drw = s_info[tick & 1][3], m_trm = s_info[tick & 1][4];
-
-    // ---- prefetch this thread's emission scores (column jcol, OPT slots)
-    float ev[OPT], pv[OPT];
-    TickDesc tdr[OPT];
-#pragma unroll
-    for (int r = 0; r < OPT; ++r) tdr[r] = tdesc[s0 + r * SSTEP];
-#pragma unroll
-    for (int r = 0; r < OPT; ++r) {
-      ev[r] = 0.f;
-      pv[r] = 0.f;
-      if (tdr[r].mode && jcol < K) {
-        ev[r] = a.emit == FV_EMIT_DENSE ? __ldg(tdr[r].erow + jcol) : __ldg(a.logB + (int64_t)jcol * a.V + tdr[r].sym);
-        if (tdr[r].first) pv[r] = __ldg(a.log_pi + jcol);
-      }
-    }
-
-    // ---- streamed: the first ring stages of this tick's logA rows
-    const int sg = lane / LJ, jg = lane % LJ;
-    const int cg = warp % CG, rg = warp / CG;
-    float2* ring = STREAM ? reinterpret_cast<float2*>(sA) + warp * NST * 2 * WC : nullptr;
-    const float2* gsrc = STREAM ? a.Ap + (int64_t)(rg * C / 2) * a.ap_stride + j0 + cg * WC : nullptr;
-    constexpr int NIT = C / 4;
-    auto issue = [&](int it) {
-      float2* dst = ring + (it % NST) * 2 * WC;
-#pragma unroll
-      for (int u = 0; u < WC / 32; ++u) {
-        const int q = lane + 32 * u, pr = q / (WC / 2), c2 = (q % (WC / 2)) * 2;
-        cp_async16(dst + pr * WC + c2, gsrc + (int64_t)(2 * it + pr) * a.ap_stride + c2);
-      }
-    };
-    if constexpr (STREAM) {
-#pragma unroll
-      for (int k = 0; k < NST - 1; ++k) {
-        if (k < NIT) issue(k);
-        cp_async_commit();
-      }
-    }
-
-    // ---- multi-CTA clusters: wait until delta_{t-1} of every CTA is here;
-    // then rank 0 sends the jobs drawn in this tick's prologue
-    if constexpr (CL > 1 && kExch != 0) {
-      if (tick > 0) {
-        const uint32_t bar = smem_addr(&s_bar[(tick - 1) & 1]);
-        const uint32_t par = (uint32_t)((tick - 1) >> 1) & 1u;
-        if (!mbar_try_wait_cluster(bar, par)) {
-          const long long w0 = clock64();
-          while (!mbar_try_wait_cluster(bar, par)) {
-            if (clock64() - w0 > kClusterWaitCycles) {
-              set_status(a.hdr, FV_ETIMEOUT, 3);
-              s_abort = 1;
-              break;
-            }
-          }
-        }
-      }
-      if (rank == 0 && tid < S && ((m_drw >> tid) & 1u)) {
-        const PJob& pj = s_pend[tid][(slots[tid].ndraw - 1) & 1];
-        const uint4* src = reinterpret_cast<const uint4*>(&pj);
-#pragma unroll
-        for (int r = 1; r < CL; ++r) {
-          const uint32_t dst = dsmem_addr(&pj, r);
-#pragma unroll
-          for (int w = 0; w < (int)(sizeof(PJob) / 16); ++w) st_async_v4(dst + 16u * w, src[w], (tick & 1) ? pBar1[r] : pBar0[r]);
-        }
-      }
-    }
-
-    // ---- termination of jobs that finished last tick (rank 0)
-    if (rank == 0 && m_trm) {
-      for (int s = warp; s < S; s += NW) {
-        if (!((m_trm >> s) & 1u)) continue;
-        const SlotFin& fs = s_fin[s];
-        const float* dl = sD + (cur * S + s) * KPS;
-        if (kind == kJobVanilla) {
-          // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q]
-          float bv = -CUDART_INF_F;
-          int bi = 0x7fffffff;
-          for (int j = lane; j < K; j += 32) {
-            const float v = dl[j + ((j >> 5) << 2)];
-            if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
-          }
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-          }
-          if (lane == 0) {
-            a.qlast[fs.b] = bi;
-            a.scores[fs.b] = dl[bi + ((bi >> 5) << 2)];
-          }
-        } else if (kind == kJobSub && lane == 0) {
-          // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
-          const int tmid = (fs.m + fs.n) / 2;
-          int q = sMid[(cur * S + s) * KP + ((unsigned)fs.q_n < (unsigned)K ? fs.q_n : 0)];
-          q = (unsigned)q < (unsigned)K ? q : 0;
-          a.paths[fs.path_off + tmid] = q;
-          a.sval[fs.aux_off + tmid] = Cfg::GSNAP ? gSnap[s * KP + q] : sSnap[s * KP + q];
-        }
-      }
-    }
-
-    // ---- sub jobs: rank 0 keeps delta_{tmid} (all K states) as the snapshot
-    if (kind == kJobSub && rank == 0 && m_snp) {
-      for (int s = 0; s < S; ++s) {
-        if (!((m_snp >> s) & 1u)) continue;
-        const float* dl = sD + (cur * S + s) * KPS;
-        float* dst = Cfg::GSNAP ? gSnap + s * KP : sSnap + s * KP;
-        for (int j = tid; j < K; j += NT) dst[j] = dl[j + ((j >> 5) << 2)];
-      }
+      tick_live = live;
     }
 
     // ---- main loop: value-only tropical product over this warp's C rows.
@@ -808,7 +741,86 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           *reinterpret_cast<float2*>(pp + 2 * LJ * g) = make_float2(acc[x][2 * g], acc[x][2 * g + 1]);
       }
     }
-    __syncthreads();
+    // every warp's partial maxima and this tick's slot descriptors are
+    // published; a tick with no live slot ends the engine
+    if (!__syncthreads_or(tick_live)) break;
+    const uint32_t m_act = s_info[tick & 1][0], m_mid = s_info[tick & 1][1], m_snp = s_info[tick & 1][2];
+    const uint32_t m_drw = s_info[tick & 1][3], m_trm = s_info[tick & 1][4];
+
+    // ---- this thread's emission scores (column jcol, OPT slots): issued
+    // now, used after the merge and re-scan, which hide their latency
+    float ev[OPT], pv[OPT];
+    TickDesc tdr[OPT];
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) tdr[r] = tdesc[s0 + r * SSTEP];
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) {
+      ev[r] = 0.f;
+      pv[r] = 0.f;
+      if (tdr[r].mode && jcol < K) {
+        ev[r] = a.emit == FV_EMIT_DENSE ? __ldg(tdr[r].erow + jcol) : __ldg(a.logB + (int64_t)jcol * a.V + tdr[r].sym);
+        if (tdr[r].first) pv[r] = __ldg(a.log_pi + jcol);
+      }
+    }
+
+    // ---- multi-CTA clusters: rank 0 sends the jobs drawn in this tick's
+    // prologue (they complete on this tick's barrier of every other CTA)
+    if constexpr (CL > 1 && kExch != 0) {
+      if (rank == 0 && tid < S && ((m_drw >> tid) & 1u)) {
+        const PJob& pj = s_pend[tid][(slots[tid].ndraw - 1) & 1];
+        const uint4* src = reinterpret_cast<const uint4*>(&pj);
+#pragma unroll
+        for (int r = 1; r < CL; ++r) {
+          const uint32_t dst = dsmem_addr(&pj, r);
+#pragma unroll
+          for (int w = 0; w < (int)(sizeof(PJob) / 16); ++w) st_async_v4(dst + 16u * w, src[w], (tick & 1) ? pBar1[r] : pBar0[r]);
+        }
+      }
+    }
+
+    // ---- termination of jobs that finished last tick (rank 0)
+    if (rank == 0 && m_trm) {
+      for (int s = warp; s < S; s += NW) {
+        if (!((m_trm >> s) & 1u)) continue;
+        const SlotFin& fs = s_fin[s];
+        const float* dl = sD + (cur * S + s) * KPS;
+        if (kind == kJobVanilla) {
+          // q_{T-1} = lowest argmax_j delta_{T-1}[j]; score = delta_{T-1}[q]
+          float bv = -CUDART_INF_F;
+          int bi = 0x7fffffff;
+          for (int j = lane; j < K; j += 32) {
+            const float v = dl[j + ((j >> 5) << 2)];
+            if (bi == 0x7fffffff || v > bv) { bv = v; bi = j; }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi != 0x7fffffff && (bi == 0x7fffffff || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+          }
+          if (lane == 0) {
+            a.qlast[fs.b] = bi;
+            a.scores[fs.b] = dl[bi + ((bi >> 5) << 2)];
+          }
+        } else if (kind == kJobSub && lane == 0) {
+          // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
+          const int tmid = (fs.m + fs.n) / 2;
+          int q = sMid[(cur * S + s) * KP + ((unsigned)fs.q_n < (unsigned)K ? fs.q_n : 0)];
+          q = (unsigned)q < (unsigned)K ? q : 0;
+          a.paths[fs.path_off + tmid] = q;
+          a.sval[fs.aux_off + tmid] = Cfg::GSNAP ? gSnap[s * KP + q] : sSnap[s * KP + q];
+        }
+      }
+    }
+
+    // ---- sub jobs: rank 0 keeps delta_{tmid} (all K states) as the snapshot
+    if (kind == kJobSub && rank == 0 && m_snp) {
+      for (int s = 0; s < S; ++s) {
+        if (!((m_snp >> s) & 1u)) continue;
+        const float* dl = sD + (cur * S + s) * KPS;
+        float* dst = Cfg::GSNAP ? gSnap + s * KP : sSnap + s * KP;
+        for (int j = tid; j < K; j += NT) dst[j] = dl[j + ((j >> 5) << 2)];
+      }
+    }
 
     // ---- merge: per output, the first warp whose partial is the maximum
     const int nxt = cur ^ 1;
