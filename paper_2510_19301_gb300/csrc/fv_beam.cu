@@ -2,7 +2,9 @@
 //
 // One CTA (1024 threads; 128 or 256 for small dense steps) runs one job at
 // a time (a whole sequence, or one Alg. 1 segment task) and pops the next
-// job from a global counter.  A beam
+// job from a global counter.  Beams of at least 64 states on large CSR state
+// spaces (P = 0) instead spread each sequence over a cluster of CTAs
+// (beam_csr_cluster_kernel, below).  A beam
 // is the top-B finite candidates under (score desc, state id asc); it is
 // kept sorted by state id so that the next step visits its sources in
 // ascending order.  Per step:
@@ -822,6 +824,303 @@ __global__ void __launch_bounds__(kBeamThreads, 1) beam_kernel(BeamArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Dynamic beam on CSR transitions with one sequence spread over a cluster of
+// kCB CTAs (kJobBeam, large K).  The single-CTA kernel above keeps one SM
+// busy per sequence and is bound by the latency of each step's phases; here
+// every phase is split kCB ways:
+//  * scatter: CTA r relaxes the out-edges of its share of the beam entries
+//    (64-bit atomicMax on the cluster's key array in global memory, the
+//    same keys as above) and marks each target in the bitmap of the CTA
+//    that owns the target's id range (distributed shared memory);
+//  * candidates: CTA r lists the touched targets of its id range (ids
+//    [r R, (r+1) R)) in shared memory, in id order, with c_j = M_j + E_t[j];
+//  * top-B select: the MSB radix select of the single-CTA kernel with every
+//    pass's 256-bin histogram summed over the cluster (each CTA reads the
+//    others' histograms through distributed shared memory), so every CTA
+//    takes the same threshold; keys equal to the threshold go to the lowest
+//    ids first, i.e. to the lower ranks first;
+//  * gather: each CTA learns how many winners the lower ranks hold and
+//    writes its own at that offset, in id order -- the next beam, sorted by
+//    id, in global memory, with the step's backpointers.
+// Result: the same beams, paths and scores as the single-CTA kernel.
+constexpr int kCB = 8;              // CTAs per sequence (portable cluster size)
+constexpr int kCBThreads = 1024;
+
+__device__ inline void dsmem_red_or(uint32_t addr, uint32_t v) {
+  asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ inline uint32_t dsmem_ld_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// ids per rank, its bitmap words and the shared-memory layout
+__host__ __device__ inline int cb_range(int K) { return (K + kCB - 1) / kCB; }
+__host__ __device__ inline size_t cb_smem_bytes(int K) {
+  const size_t R = (size_t)cb_range(K), bm = ((R + 31) / 32 + 3) / 4 * 4;
+  return 4 * (bm + 2 * R + 3 * 256 + 4 * kCB + 16);
+}
+
+__global__ void __launch_bounds__(kCBThreads, 1) beam_csr_cluster_kernel(BeamArgs a) {
+  extern __shared__ __align__(16) uint32_t csm[];
+  __shared__ int red[32];
+  __shared__ int misc[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const uint32_t rank = cluster_ctarank();
+  const int K = a.K, R = cb_range(K);
+  const int j_lo = (int)rank * R, j_hi = min(K, j_lo + R), nloc = max(0, j_hi - j_lo);
+  const int bm_words = ((R + 31) / 32 + 3) / 4 * 4;
+  uint32_t* bitmap = csm;                                            // [bm_words] touched, local ids
+  float* lval = reinterpret_cast<float*>(bitmap + bm_words);         // [R] listed candidate values
+  int32_t* lid = reinterpret_cast<int32_t*>(lval + R);               // [R] their ids, ascending
+  int* hist = reinterpret_cast<int*>(lid + R);                       // [2][256] this CTA's histograms
+  int* cnt = hist + 512;                                             // [4][kCB] counts from every rank
+  int* htot = cnt + 4 * kCB;                                         // [256] the cluster's histogram
+  const int cl = blockIdx.x / kCB, ncl = gridDim.x / kCB;
+  // the cluster's key array and beams: the scratch slice of its rank-0 CTA
+  char* base = a.scratch + (size_t)(cl * kCB) * a.scratch_stride;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(base);
+  base += align_up((size_t)K * 8);
+  base += 2 * align_up((size_t)K * 4);  // (cval, cslot: unused here)
+  int32_t* bid[2];
+  float* bval[2];
+  for (int q = 0; q < 2; ++q) {
+    bid[q] = reinterpret_cast<int32_t*>(base);
+    base += align_up((size_t)a.Bcap * 4);
+    bval[q] = reinterpret_cast<float*>(base);
+    base += align_up((size_t)a.Bcap * 4);
+    base += 2 * align_up((size_t)a.Bcap * 4);  // (mid, src: unused here)
+  }
+  if (a.hdr->status != 0) return;  // read by every CTA before any work: a cluster-uniform decision
+  for (int w = tid; w < bm_words; w += blockDim.x) bitmap[w] = 0u;
+  for (int j = j_lo + tid; j < j_hi; j += blockDim.x) keys[j] = 0ull;
+  cluster_sync_all();
+
+  // each thread's contiguous piece of this rank's ids / of the list
+  const int per = (R + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int t0 = min(nloc, tid * per), t1 = min(nloc, t0 + per);
+
+  // publish v to slot [which][rank] of every rank, then (after a cluster
+  // barrier) read the kCB values
+  auto publish = [&](int which, int v) {
+    if (tid < kCB) dsmem_st_u32(dsmem_addr(&cnt[which * kCB + (int)rank], (uint32_t)tid), (uint32_t)v);
+  };
+
+  // top-W of the list (n entries; values lval, ids lid, ascending) over the
+  // whole cluster -> beam buffer q at its global positions; returns the new
+  // beam size (identical in every CTA).  Writes backpointers of step t when
+  // bp_t >= 0 (source slot from the key, 0 at t = m).
+  auto select_gather = [&](int n, int W, int q, int bp_t, bool from_keys, const Job& jb) -> int {
+    const int e0 = min(n, tid * ((n + (int)blockDim.x - 1) / (int)blockDim.x));
+    const int e1 = min(n, e0 + (n + (int)blockDim.x - 1) / (int)blockDim.x);
+    int fin = 0;
+    for (int e = e0; e < e1; ++e) fin += isfinite(lval[e]) ? 1 : 0;
+    fin = block_sum(fin, red);
+    publish(0, fin);
+    cluster_sync_all();
+    int total = 0;
+    for (int r = 0; r < kCB; ++r) total += cnt[0 * kCB + r];
+    const bool all = total <= W;
+    uint32_t thr = 0u;
+    int need_eq = 0;
+    if (!all) {
+      uint32_t prefix = 0u, mask = 0u;
+      int remaining = W;
+      for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        int* h = hist + (pass & 1) * 256;
+        for (int k = tid; k < 256; k += blockDim.x) h[k] = 0;
+        __syncthreads();
+        for (int e = tid; e < n; e += blockDim.x) {
+          const float c = lval[e];
+          if (!isfinite(c)) continue;
+          const uint32_t u = ord_key(c);
+          if ((u & mask) == prefix) atomicAdd(&h[(u >> shift) & 0xFFu], 1);
+        }
+        for (int k = tid; k < 256; k += blockDim.x) htot[k] = 0;
+        cluster_sync_all();  // every rank's histogram of this pass is complete
+        // the cluster's histogram: every thread adds a few (rank, digit)
+        // counts read from the other CTAs, so the remote loads overlap
+        for (int x = tid; x < 256 * kCB; x += blockDim.x) {
+          const int d = x & 255, r = x >> 8;
+          const int v = (int)dsmem_ld_u32(dsmem_addr(&h[d], (uint32_t)r));
+          if (v) atomicAdd(&htot[d], v);
+        }
+        __syncthreads();
+        if (tid < 32) {
+          int hv[8], sum = 0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            hv[u] = htot[255 - 8 * lane - u];
+            sum += hv[u];
+          }
+          int incl = sum;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int excl = incl - sum;
+          if (excl < remaining && remaining <= incl) {
+            int acc = excl, d = 255 - 8 * lane - 7;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (acc + hv[u] >= remaining) { d = 255 - 8 * lane - u; break; }
+              acc += hv[u];
+            }
+            misc[0] = d;
+            misc[1] = remaining - acc;
+          }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)misc[0] << shift;
+        mask |= 0xFFu << shift;
+        remaining = misc[1];
+        __syncthreads();
+      }
+      thr = prefix;
+      need_eq = remaining;
+    }
+    // winners of this rank: keys above the threshold, and keys equal to it
+    // while the lower ranks have not taken the needed number
+    int n_gt = 0, n_eq = 0;
+    for (int e = e0; e < e1; ++e) {
+      const float c = lval[e];
+      if (!isfinite(c)) continue;
+      const uint32_t u = ord_key(c);
+      if (all || u > thr) ++n_gt;
+      else if (u == thr) ++n_eq;
+    }
+    int tot_eq_loc, tot_gt_loc;
+    const int eq_before_loc = block_scan(n_eq, red, &tot_eq_loc);
+    block_scan(n_gt, red, &tot_gt_loc);
+    publish(1, tot_gt_loc);
+    publish(2, tot_eq_loc);
+    cluster_sync_all();
+    int eq_before = 0, win_before = 0, nb = 0;
+    for (int r = 0; r < kCB; ++r) {
+      const int gt_r = cnt[1 * kCB + r], eq_r = cnt[2 * kCB + r];
+      const int take_r = min(max(need_eq - eq_before, 0), eq_r);
+      if (r < (int)rank) win_before += gt_r + take_r;
+      if (r == (int)rank) misc[2] = take_r;
+      eq_before += eq_r;
+      nb += gt_r + take_r;
+    }
+    __syncthreads();
+    const int take_rank = misc[2];
+    const int take_eq = min(max(take_rank - eq_before_loc, 0), n_eq);
+    int tot;
+    int o = win_before + block_scan(n_gt + take_eq, red, &tot);
+    int eq_seen = 0;
+    for (int e = e0; e < e1; ++e) {
+      const float c = lval[e];
+      if (!isfinite(c)) continue;
+      const uint32_t u = ord_key(c);
+      bool take = all || u > thr;
+      if (!take && u == thr) take = (eq_seen++ < take_eq);
+      if (!take) continue;
+      const int j = lid[e];
+      bid[q][o] = j;
+      bval[q][o] = c;
+      if (bp_t >= 0) {
+        const int sl = from_keys ? (int)(0xFFFFFFFFull - (keys[j] & 0xFFFFFFFFull)) : 0;
+        a.bp_id[jb.aux_off + (int64_t)bp_t * a.Wcap + o] = j;
+        a.bp_src[jb.aux_off + (int64_t)bp_t * a.Wcap + o] = sl;
+      }
+      ++o;
+    }
+    __syncthreads();  // every thread has read its winners' keys before any is cleared
+    return nb;
+  };
+
+  for (int jk = cl; jk < a.order_count; jk += ncl) {
+    const int b = a.order[a.order_begin + jk];
+    const Job jb = a.jobs[b];
+    const int T = jb.T;
+    const int W = a.Wcap < a.Bcap ? a.Wcap : a.Bcap;
+    // ---- t = 0: every state of this rank's range is a candidate
+    int n = 0;
+    {
+      int tot;
+      const int o0 = block_scan(t1 - t0, red, &tot);
+      for (int x = t0; x < t1; ++x) {
+        const int j = j_lo + x;
+        lval[o0 + x - t0] = __fadd_rn(__ldg(a.log_pi + j), beam_emit(a, jb, 0, j));
+        lid[o0 + x - t0] = j;
+      }
+      n = tot;
+      __syncthreads();
+    }
+    int p = 0;
+    int nb = select_gather(n, W, p, 0, false, jb);
+    cluster_sync_all();  // beam 0 is complete in global memory
+    bool infeasible = nb == 0;
+    for (int t = 1; t < T && !infeasible; ++t) {
+      // the next step's emission row goes to L2 while this one is used
+      if (a.emit == FV_EMIT_DENSE && tid == 0 && rank == 0 && t + 1 < T && (K & 3) == 0) {
+        const float* row = a.E + jb.e_off + (int64_t)(t + 1) * K;
+        if (((uintptr_t)row & 15u) == 0) prefetch_l2_bulk(row, (uint32_t)K * 4u);
+      }
+      // ---- scatter this rank's share of the beam entries
+      const int s0 = (int)(((int64_t)nb * rank) / kCB), s1 = (int)(((int64_t)nb * (rank + 1)) / kCB);
+      for (int k = s0 + warp; k < s1; k += nwarp) {
+        const int i = bid[p][k];
+        const float v = bval[p][k];
+        for (int e = a.row_ptr[i] + lane; e < a.row_ptr[i + 1]; e += 32) {
+          const int j = a.col[e];
+          const float c = __fadd_rn(v, a.val[e]);
+          const unsigned long long key = ((unsigned long long)ord_key(c) << 32) | (0xFFFFFFFFull - (unsigned)k);
+          atomicMax(&keys[j], key);
+          const int ow = j / R, jl = j - ow * R;
+          dsmem_red_or(dsmem_addr(&bitmap[jl >> 5], (uint32_t)ow), 1u << (jl & 31));
+        }
+      }
+      cluster_sync_all();  // keys and bitmaps of this step are complete
+      // ---- candidates of this rank's ids, listed in id order
+      {
+        int c_n = 0;
+        for (int x = t0; x < t1; ++x) c_n += (bitmap[x >> 5] >> (x & 31)) & 1u;
+        int tot;
+        int o = block_scan(c_n, red, &tot);
+        for (int x = t0; x < t1; ++x) {
+          if (!((bitmap[x >> 5] >> (x & 31)) & 1u)) continue;
+          const int j = j_lo + x;
+          const unsigned long long key = keys[j];
+          const int sl = (int)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+          float m = ord_value((uint32_t)(key >> 32));
+          if (m == 0.0f) m = __fadd_rn(bval[p][sl], beam_csr_w(a, bid[p][sl], j));
+          lval[o] = __fadd_rn(m, beam_emit(a, jb, t, j));
+          lid[o] = j;
+          ++o;
+        }
+        n = tot;
+        __syncthreads();
+      }
+      const int np = p ^ 1;
+      nb = select_gather(n, W, np, t, true, jb);
+      // ---- clear this rank's keys and bitmap
+      for (int e = tid; e < n; e += blockDim.x) keys[lid[e]] = 0ull;
+      for (int w = tid; w < bm_words; w += blockDim.x) bitmap[w] = 0u;
+      cluster_sync_all();  // the next beam is complete; keys and bitmaps are clear
+      p = np;
+      if (nb == 0) infeasible = true;
+    }
+    if (!infeasible) {
+      if (rank == 0 && tid == 0) {
+        int kb = 0;  // best final entry: highest score, lowest id
+        for (int e = 1; e < nb; ++e)
+          if (bval[p][e] > bval[p][kb]) kb = e;
+        a.scores[b] = bval[p][kb];
+        a.qlast[b] = kb;
+      }
+    } else if (rank == 0 && tid == 0) {
+      set_status(a.hdr, FV_EINFEASIBLE, (uint32_t)b);
+    }
+    cluster_sync_all();
+  }
+}
+
 // Backtrack through per-step beam backpointers (one thread per sequence).
 __global__ void beam_backtrack_kernel(const Job* jobs, const int32_t* order, int32_t begin, int32_t count,
                                       int32_t Wcap, const int32_t* bp_id, const int32_t* bp_src,
@@ -874,10 +1173,50 @@ __global__ void beam_resolve_kernel(const Job* jobs, const int32_t* order, int32
   }
 }
 
+// Large CSR beams (P = 0): one cluster of kCB CTAs per sequence when the
+// device can hold such a cluster; 0 when launched, 1 when not applicable.
+static int launch_beam_cluster(const BeamArgs& a, int max_jobs, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (a.trans != FV_TRANS_CSR || a.kind != kJobBeam || a.static_beam || a.K < 8192) return 1;
+  if (a.Wcap < 64) return 1;  // narrow beams: one CTA per sequence has less per-step latency
+  const size_t smem = cb_smem_bytes(a.K);
+  if (smem > (size_t)200 * 1024) return 1;
+  int clusters = a.max_ctas / kCB;
+  if (max_jobs < clusters) clusters = max_jobs;
+  if (clusters < 1) return 1;
+  if (cudaFuncSetAttribute(beam_csr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 1;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCB;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kCBThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(kCB * clusters);
+  int resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, beam_csr_cluster_kernel, &cfg) != cudaSuccess || resident < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (clusters > resident) cfg.gridDim = dim3(kCB * resident);
+  *err = cudaLaunchKernelEx(&cfg, beam_csr_cluster_kernel, a);
+  return 0;
+}
+
 cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  {
+    cudaError_t ce;
+    if (launch_beam_cluster(a, max_jobs, st, &ce) == 0) return ce;
+  }
   BeamArgs b = a;
   size_t smem = sizeof(uint32_t) * beam_bitmap_words(a.K);
   const size_t beam_bytes = sizeof(int32_t) * 10 * (size_t)a.Bcap;

@@ -110,3 +110,27 @@ def test_csr_subtask_rerun_matches_oracle(fv):
     reruns = [oracle.flash_bs(hmm, e, 4, 2)[2] for e in E_list]
     assert sum(reruns) > 0, "case does not exercise the re-run"
     run_beam(fv, m, hmm, E_list, 2, 4)
+
+
+@pytest.mark.parametrize("K,deg", [(8192, 4), (10001, 32)])
+@pytest.mark.parametrize("B", [1, 64, 256, 1000, 4000])
+def test_csr_beam_large_k_cluster_engine(fv, K, deg, B):
+    """Large CSR state spaces (K >= 8192, P = 0) run one sequence per
+    cluster of CTAs when the beam holds at least 64 states (id ranges
+    split over the CTAs, cluster-wide top-B), narrower beams one CTA:
+    same results as the oracle, including ranges of unequal size (K not a
+    multiple of the cluster size) and ties between ranks (integer weights
+    and emissions)."""
+    rng = np.random.default_rng(K + B)
+    rp, col, val = W.random_csr(K, deg, rng)
+    log_pi = W._log_dirichlet(rng, 1.0, (K,)).astype(np.float32)
+    lengths = [1, 2, 50, 300]
+    E_list = [W.gaussian_emissions(int(t), K, rng) for t in lengths]
+    m, hmm = make_model(fv, log_pi, csr=(rp, col, val))
+    run_beam(fv, m, hmm, E_list, B, 0)
+    # integer data: many equal candidates, resolved by the lowest id
+    val_i = np.round(val * 2).astype(np.float32)
+    lp_i = np.round(log_pi).astype(np.float32)
+    E_i = [np.round(e).astype(np.float32) for e in E_list]
+    m2, hmm2 = make_model(fv, lp_i, csr=(rp, col, val_i))
+    run_beam(fv, m2, hmm2, E_i, B, 0)
