@@ -197,6 +197,25 @@ def time_decoder(dec, steps, warmup, lib):
     return e0.elapsed_time(e1) / steps, tot.value / max(steps, 1)
 
 
+def flash_phases(dec, lib):
+    """One FLASH decode with the library's timing pairs: the root pass (with
+    its resolve), then every task level of Alg. 1 (a budget decode's last
+    level is its leaf waves).  Returns the milliseconds per phase."""
+    import ctypes
+
+    import torch
+    torch.cuda.synchronize()
+    lib.fv_timing_enable(1)
+    dec.launch()
+    buf = (ctypes.c_float * 256)()
+    n = ctypes.c_int32(0)
+    lib.fv_timing_pairs(buf, 256, ctypes.byref(n))
+    lib.fv_timing_enable(0)
+    ms = [float(buf[i]) for i in range(n.value)]
+    return {"root_pass_ms": ms[0] if ms else None, "task_level_ms": ms[1:],
+            "levels": max(0, len(ms) - 1)}
+
+
 def per_sequence_comparator(fv, m, lengths, E, K, n_sample, device):
     """Plain GPU Viterbi: the same exact decoder launched once per sequence
     (one sequence per call, one stream), timed on a sample of sequences."""
@@ -443,6 +462,10 @@ def config3_dense(fv, T, device, lib):
         res[name] = d
         out[name] = {"ms": ms, "value": n * T * K / (ms / 1e3), "unit": UNIT, "workspace_bytes": d.ws_bytes,
                      "forward_kernels_ms": fwd}
+    ph = flash_phases(res["flash_P16_budget_1_16"], lib)
+    ph["leaf_waves_ms"] = ph["task_level_ms"][-1] if ph["task_level_ms"] else None
+    ph["root_vs_vanilla_forward"] = ph["root_pass_ms"] / out["vanilla"]["forward_kernels_ms"]
+    out["flash_P16_budget_1_16"]["phases"] = ph
     pv, sv = res["vanilla"].paths, res["vanilla"].scores
     pf, sf = res["flash_P16_budget_1_16"].paths, res["flash_P16_budget_1_16"].scores
     out["flash_P16_budget_1_16"]["bit_identical_to_vanilla"] = bool(
@@ -790,7 +813,11 @@ def run_ours(args):
         db = fv.Decoder([m], batch, mode="flash", P=16, mem_budget=table // 16)
         db(check=True)
         bms, _ = time_decoder(db, max(2, args.steps // 20), 2, lib)
+        ph = flash_phases(db, lib)
+        ph["leaf_waves_ms"] = ph["task_level_ms"][-1] if ph["task_level_ms"] else None
+        ph["root_vs_vanilla"] = ph["root_pass_ms"] / fwd_ms if ph["root_pass_ms"] else None
         modes["flash_P16_budget_1_16"] = {
+            "phases": ph,
             "value": state_steps / (bms / 1e3), "unit": UNIT, "ms_per_step": bms, "time_vs_vanilla": bms / ms,
             "bit_identical_to_vanilla": bool(torch.equal(dec.paths, db.paths) and torch.equal(
                 dec.scores.view(torch.int32), db.scores.view(torch.int32))),

@@ -218,14 +218,20 @@ const char* fv_status_str(fv_status s);
 fv_status fv_path_score(const fv_model* models, int32_t n_models, const fv_batch* batch,
                         const int32_t* paths, float* scores_out, fv_stream_t stream);
 
-/* Optional timing of the main decode kernel, for roofline reports.  While
- * enabled, every fv_decode records a CUDA event pair (library-owned, at most
+/* Optional timing of the main decode kernels, for roofline reports.  While
+ * enabled, every fv_decode records CUDA event pairs (library-owned, at most
  * 256 pairs) around its main decode kernel launches on the call's stream.
  * fv_timing_read synchronises on the recorded pairs and returns the total
  * elapsed milliseconds and the number of pairs since the last reset. */
 fv_status fv_timing_enable(int32_t on);
 fv_status fv_timing_reset(void);
 fv_status fv_timing_read(float* total_ms, int32_t* n_pairs);
+/* The recorded pairs one by one (milliseconds each, in recording order, at
+ * most max_pairs; *n_pairs = how many were written).  A FLASH decode records
+ * one pair for its root pass (with the resolve) and one per task level of
+ * Alg. 1 (the budget-leaf waves of the leaf level together); the other
+ * modes one pair per decode.  Synchronises on the recorded pairs. */
+fv_status fv_timing_pairs(float* ms, int32_t max_pairs, int32_t* n_pairs);
 
 /* Autotuning of the exact forward engine (not in the paper).  Dense exact
  * decoding has, per class of K (<= 64, <= 128, <= 256), several engine

@@ -119,6 +119,8 @@ def load(build_if_missing: bool = False):
     lib.fv_timing_enable.restype = ctypes.c_int
     lib.fv_timing_reset.argtypes = []
     lib.fv_timing_reset.restype = ctypes.c_int
+    lib.fv_timing_pairs.argtypes = [P, i32, P]
+    lib.fv_timing_pairs.restype = ctypes.c_int
     lib.fv_timing_read.argtypes = [P, P]
     lib.fv_timing_read.restype = ctypes.c_int
     lib.fv_decode_noalloc.argtypes = [MP, i32, BP, P, P, P]

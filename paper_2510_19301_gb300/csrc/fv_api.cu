@@ -798,8 +798,12 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
     if (fp.levels[m] > 0 &&
         launch_level1_tasks(jobs, order, R.begin[m], R.count[m], p->P, lists[0], &counts[0], tmp, st) != cudaSuccess)
       return FV_ECUDA;
+    // timing pairs: the root pass (with its resolve), then one per task
+    // level, the budget-leaf waves together
+    timed_end(st);
     int c = 0;
     for (int lvl = 0; lvl < fp.levels[m]; ++lvl) {
+      timed_begin(st);
       if (lvl == fp.leaf_level[m]) {
         // budget leaves: every task of this level keeps its own
         // backpointer rows; waves of tasks whose rows fit the budget
@@ -823,6 +827,7 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
             return FV_ECUDA;
         }
         da.task_first = nullptr;
+        timed_end(st);
         break;
       }
       if (launch_reset(da.pop, st) != cudaSuccess) return FV_ECUDA;
@@ -836,8 +841,8 @@ fv_status fv_decode(const fv_model* models, int32_t n_models, const fv_batch* ba
                              nullptr, st) != cudaSuccess)
         return FV_ECUDA;
       c ^= 1;
+      timed_end(st);
     }
-    timed_end(st);
   }
   return FV_OK;
 }
@@ -985,6 +990,17 @@ fv_status fv_timing_enable(int32_t on) {
 
 fv_status fv_timing_reset(void) {
   g_timed = 0;
+  return FV_OK;
+}
+
+fv_status fv_timing_pairs(float* ms, int32_t max_pairs, int32_t* n_pairs) {
+  if (!ms || !n_pairs || max_pairs < 0) return FV_EINVAL;
+  const int n = g_timed < max_pairs ? g_timed : max_pairs;
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventSynchronize(g_ev[2 * i + 1]) != cudaSuccess) return FV_ECUDA;
+    if (cudaEventElapsedTime(&ms[i], g_ev[2 * i], g_ev[2 * i + 1]) != cudaSuccess) return FV_ECUDA;
+  }
+  *n_pairs = n;
   return FV_OK;
 }
 
