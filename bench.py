@@ -37,7 +37,7 @@ WORKLOAD = "batched-uneven: 1024 seqs, K=256 dense FP32, T~U[500,4000], E=log_so
 # x 8-column configuration the autotuner picks on this batch): reads of E
 # plus writes of psi, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of a 128-sequence launch of this workload.
-DRAM_BYTES_PER_STATE_STEP = (279438336 + 110472192) / (271316 * 256)
+DRAM_BYTES_PER_STATE_STEP = (278595072 + 109117696) / (271316 * 256)
 
 
 def dist_env():
