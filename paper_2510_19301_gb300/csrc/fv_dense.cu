@@ -1343,7 +1343,7 @@ int dense_variants(int K) {
     case 0: return 3;
     case 1: return 2;
     case 2: return 3;
-    case 3: return 2;
+    case 3: return 3;
     case 4: return 2;
     default: return 1;
   }
@@ -1375,8 +1375,13 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);
   }
   if (a.K <= 512) {
-    if (v == 1) return launch_dense_cfg<128, 8, 16, 4, 512, true, 4>(a, max_clusters, st);
-    return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
+    // default: 8-CTA clusters of 64 columns each, so every CTA's slab of
+    // logA (512 rows x 64 columns) stays in shared memory (measured: half
+    // the time of the streamed 4-CTA configurations, 256 sequences);
+    // variants 1 and 2 stream 128-column slabs from L2
+    if (v == 2) return launch_dense_cfg<128, 8, 16, 4, 512, true, 4>(a, max_clusters, st);
+    if (v == 1) return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
+    return launch_dense_cfg<64, 8, 16, 8, 512, false, 4>(a, max_clusters, st);
   }
   if (v == 1) return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4>(a, max_clusters, st);
   return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);

@@ -15,11 +15,22 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("K", [1100, 300, 1000])
-def test_withheld_step_times_out_and_context_survives(K):
+@pytest.mark.parametrize("K,variant", [(1100, 0), (300, 0), (300, 1), (1000, 0)])
+def test_withheld_step_times_out_and_context_survives(K, variant):
+    """K=300: variant 0 is the resident 8-CTA cluster configuration of the
+    K <= 512 class, variant 1 the streamed 4-CTA one; both exchange delta
+    through mbarriers."""
     import paper_2510_19301_gb300 as fv
     from paper_2510_19301_gb300 import _lib as L
     fv._lib.load(build_if_missing=True)
+    fv.set_engine_variant(K, variant)
+    try:
+        _withhold_case(fv, L, K)
+    finally:
+        fv.set_engine_variant(K, 0)
+
+
+def _withhold_case(fv, L, K):
     rng = np.random.default_rng(77 + K)
     log_pi, logA = W.random_model(K, rng)
     lengths = [5, 9, 3]
