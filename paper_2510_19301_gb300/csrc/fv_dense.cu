@@ -228,7 +228,12 @@ constexpr long long kClusterWaitCycles = 1ll << 31;
 // holds 4 slots x TW columns; a warp covers all S slots and LJ*TW columns;
 // CG warps side by side cover the CTA's J columns and RG = NW/CG row groups
 // split the rows.
-template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8>
+// DEFER: the exact re-scan of a tick runs after the tick's delta has been
+// sent (its latency then overlaps the exchange) -- for jobs without
+// MidState (vanilla, budget leaves, checkpoint passes); a third delta buffer
+// keeps the re-scanned rows intact while the other CTAs already write the
+// next tick's delta, and the MidState buffers are left out.
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, bool DEFER = false>
 struct DenseCfg {
   static constexpr int NT = NW * 32;
   static constexpr int LS = S / 4;        // slot groups per warp
@@ -246,6 +251,8 @@ struct DenseCfg {
   static constexpr int CH = STREAM ? (KPM <= 512 ? 8 : 16) : C;
   static constexpr int NST = KPM <= 512 ? 8 : 5;  // streamed: ring stages of 4 rows per warp
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
+  static constexpr int NDB = DEFER ? 3 : 2;   // delta buffers
+  static constexpr int NMID = DEFER ? 0 : 2;  // MidState buffers
   static_assert(LJ * LS == 32 && LS * 4 == S && (TW == 8 || TW == 4), "lane tile is 4 sequences x TW columns");
   static_assert(J % WC == 0 && NW % CG == 0 && WC % 32 == 0, "warp tiling");
   static_assert((S * J) % NT == 0 && NT % J == 0, "epilogue: one column per thread, OPT slots");
@@ -258,17 +265,19 @@ struct DenseCfg {
   // the rest (streamed engines and wide row-group splits keep them in the
   // workspace, one row of KP floats per slot of each cluster)
   static constexpr bool GSNAP =
-      STREAM || (a_floats + 2ull * S * KPS + (size_t)RG * S * J + (size_t)S * KP) * sizeof(float) +
-                        2ull * S * KP * sizeof(uint16_t) > (size_t)220 * 1024;
+      STREAM || (a_floats + (size_t)NDB * S * KPS + (size_t)RG * S * J + (size_t)S * KP) * sizeof(float) +
+                        (size_t)NMID * S * KP * sizeof(uint16_t) > (size_t)220 * 1024;
   static constexpr size_t snap_floats = GSNAP ? 0 : (size_t)S * KP;
   static constexpr size_t smem_bytes =
-      sizeof(float) * (a_floats + 2ull * S * KPS + (size_t)RG * S * J + snap_floats) +
-      sizeof(uint16_t) * 2ull * S * KP + (STREAM ? (size_t)RG * S * J : 0);
+      sizeof(float) * (a_floats + (size_t)NDB * S * KPS + (size_t)RG * S * J + snap_floats) +
+      sizeof(uint16_t) * (size_t)NMID * S * KP + (STREAM ? (size_t)RG * S * J : 0);
 };
 
-template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW, bool DEFER>
 __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
+  constexpr int NDB = Cfg::NDB;
+  static_assert(!DEFER || (!STREAM && CL > 1), "deferred re-scan: resident multi-CTA configurations");
   constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT, KP = Cfg::KP, C = Cfg::C, KPS = Cfg::KPS;
   constexpr int CG = Cfg::CG, RG = Cfg::RG, WC = Cfg::WC;
   constexpr int CH = Cfg::CH, NST = Cfg::NST;
@@ -292,11 +301,11 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   // A[i+1][j0+jj]); streamed: each warp's ring of row-pair stages, filled
   // with cp.async from the row-pair copy a.Ap in global memory
   float* sA = smem;                           // resident [KP/2][J] / streamed [NW][NST][2][J] float2
-  float* sD = sA + Cfg::a_floats;             // [2][S][KPS] delta per slot, skewed rows
-  float* sPart = sD + 2 * S * KPS;            // [RG][S][J]  per-row-group partial maxima
+  float* sD = sA + Cfg::a_floats;             // [NDB][S][KPS] delta per slot, skewed rows
+  float* sPart = sD + NDB * S * KPS;          // [RG][S][J]  per-row-group partial maxima
   float* sSnap = sPart + RG * S * J;          // resident [S][KP] sub: delta at t_mid
   uint16_t* sMid = reinterpret_cast<uint16_t*>(sSnap + Cfg::snap_floats);  // [2][S][KP] MidState
-  uint8_t* sPC = reinterpret_cast<uint8_t*>(sMid + 2 * S * KP);            // streamed [RG][S][J] chunk
+  uint8_t* sPC = reinterpret_cast<uint8_t*>(sMid + Cfg::NMID * S * KP);   // streamed [RG][S][J] chunk
   const float2* sA2 = reinterpret_cast<const float2*>(sA);
   // streamed: global snapshot rows of this cluster's slots (sub jobs)
   float* gSnap = Cfg::GSNAP ? a.snap_scratch + (size_t)(blockIdx.x / CL) * S * KP : nullptr;
@@ -324,8 +333,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       sA[x] = (i < K && j < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
     }
   }
-  for (int x = tid; x < 2 * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
-  for (int x = tid; x < 2 * S * KP; x += NT) sMid[x] = 0;
+  for (int x = tid; x < NDB * S * KPS; x += NT) sD[x] = -CUDART_INF_F;
+  for (int x = tid; x < Cfg::NMID * S * KP; x += NT) sMid[x] = 0;
 
   // next job for the slot: rank 0 draws an index from the shared counter and
   // reads the job (other CTAs receive it)
@@ -801,7 +810,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
             a.qlast[fs.b] = bi;
             a.scores[fs.b] = dl[bi + ((bi >> 5) << 2)];
           }
-        } else if (kind == kJobSub && lane == 0) {
+        } else if (!DEFER && kind == kJobSub && lane == 0) {
           // Alg. 2 output: q*_{tmid} = MidState[q*_n]; its delta from the snapshot
           const int tmid = (fs.m + fs.n) / 2;
           int q = sMid[(cur * S + s) * KP + ((unsigned)fs.q_n < (unsigned)K ? fs.q_n : 0)];
@@ -823,7 +832,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
     }
 
     // ---- merge: per output, the first warp whose partial is the maximum
-    const int nxt = cur ^ 1;
+    const int nxt = cur + 1 < NDB ? cur + 1 : 0;
     float best[OPT], val[OPT];
     int wbase[OPT], arg[OPT];
 #pragma unroll
@@ -853,8 +862,11 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       arg[r] = wb * CH;
     }
     // ---- exact argmax: rows of the winning chunk, descending, so the last
-    // match is the lowest row; the kept value is the recomputed candidate
-    {
+    // match is the lowest row; the kept value is the recomputed candidate.
+    // Deferred configurations run it right away only for a zero maximum
+    // (its sign is the lowest maximising row's) and otherwise after the
+    // tick's delta has been sent.
+    auto rescan = [&]() {
       const float* dr[OPT];
       const float2* ar[OPT];
       const int64_t astr = STREAM ? a.ap_stride : J;
@@ -927,6 +939,18 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
           }
         }
       }
+    };
+    bool rescanned = false;
+    if constexpr (DEFER) {
+      bool zero = false;
+#pragma unroll
+      for (int r = 0; r < OPT; ++r) zero |= best[r] == 0.0f;
+      if (zero) {
+        rescan();
+        rescanned = true;
+      }
+    } else {
+      rescan();
     }
 
     // ---- + E, per-kind bookkeeping, delta_t to every CTA.  Global stores
@@ -969,7 +993,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         }
         dval = __fadd_rn(val[r], ev[r]);
       }
-      if (td.f_mid) {
+      if (!DEFER && td.f_mid) {
         const uint16_t mnew = td.f_mid == 1 ? (uint16_t)ag : sMid[(cur * S + s) * KP + ag];
         const int mo = (nxt * S + s) * KP + jcol;
         sMid[mo] = mnew;
@@ -1001,7 +1025,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
             if (rr != (int)rank) dsmem_st_v4f32(pD[rr] + 4u * dof, v.x, v.y, v.z, v.w);
         }
       }
-      if (m_mid) {
+      if (!DEFER && m_mid) {
 #pragma unroll
         for (int r0 = 0; r0 < OPT; r0 += 8) {
           const int r = r0 + lane / 4;
@@ -1051,7 +1075,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
             if (rr != (int)rank) st_async_v4(pD[rr] + 4u * dof, v, (tb ? pBar1[rr] : pBar0[rr]));
         }
       }
-      if (m_mid) {
+      if (!DEFER && m_mid) {
 #pragma unroll
         for (int r0 = 0; r0 < OPT; r0 += 8) {
           const int r = r0 + lane / 4;
@@ -1067,6 +1091,16 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       }
     } else {
       __syncthreads();
+    }
+    if constexpr (DEFER) {
+      // the deferred re-scan (delta_t is on its way to the other CTAs)
+      uint32_t psi_bits = 0;
+#pragma unroll
+      for (int r = 0; r < OPT; ++r) psi_bits |= st_mask & (1u << (2 * r));
+      if (psi_bits && !rescanned) rescan();
+#pragma unroll
+      for (int r = 0; r < OPT; ++r)
+        if (st_mask & (1u << (2 * r))) st_arg[r] = arg[r] < K ? arg[r] : 0;
     }
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
@@ -1188,10 +1222,10 @@ __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* o
 }
 
 // ------------------------------------------------------------ host launchers
-template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, bool DEFER = false>
 static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t st) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
   a.KP = KPM;
   const size_t smem = Cfg::smem_bytes;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1245,8 +1279,8 @@ template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8>
 static int dense_cfg_slots() {
   static int cached = -1;
   if (cached >= 0) return cached;
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, false>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW, false>;
   int dev = 0, nsm = 0, resident = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes) != cudaSuccess) {
@@ -1280,7 +1314,7 @@ int dense_job_slots(int K) {
   if (K <= 64) return dense_cfg_slots<64, 16, 4, 1, 64, false>();
   if (K <= 128) return dense_cfg_slots<128, 8, 16, 1, 128, false, 4>();
   if (K <= 256) return dense_cfg_slots<128, 8, 16, 2, 256, false, 4>();
-  if (K <= 512) return dense_cfg_slots<128, 8, 8, 4, 512, true>();
+  if (K <= 512) return dense_cfg_slots<64, 8, 16, 8, 512, false, 4>();
   return dense_cfg_slots<128, 8, 8, 8, 1024, true>();
 }
 
@@ -1369,6 +1403,11 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     if (v == 1) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
     return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
   }
+  // jobs without MidState (exact decoding with psi rows, budget leaves,
+  // checkpoint passes) on the resident 8-CTA configuration defer the
+  // re-scan past the delta exchange (measured: 8% less time at K=512; with
+  // the 2-CTA cluster barrier of K <= 256 it was 1-2% slower, not used)
+  const bool defer = a.kind == kJobVanilla || a.kind == kJobLeaf || (a.kind == kJobRoot && a.ckpt);
   if (a.K <= 256) {
     if (v == 2) return launch_dense_cfg<128, 8, 16, 2, 256, false, 8>(a, max_clusters, st);
     if (v == 1) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
@@ -1381,6 +1420,7 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     // variants 1 and 2 stream 128-column slabs from L2
     if (v == 2) return launch_dense_cfg<128, 8, 16, 4, 512, true, 4>(a, max_clusters, st);
     if (v == 1) return launch_dense_cfg<128, 8, 8, 4, 512, true>(a, max_clusters, st);
+    if (defer) return launch_dense_cfg<64, 8, 16, 8, 512, false, 4, true>(a, max_clusters, st);
     return launch_dense_cfg<64, 8, 16, 8, 512, false, 4>(a, max_clusters, st);
   }
   if (v == 1) return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4>(a, max_clusters, st);
