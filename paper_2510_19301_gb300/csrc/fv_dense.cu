@@ -229,7 +229,8 @@ constexpr long long kClusterWaitCycles = 1ll << 31;
 // CG warps side by side cover the CTA's J columns and RG = NW/CG row groups
 // split the rows.
 // DEFER: the exact re-scan of a tick runs after the tick's delta has been
-// sent (its latency then overlaps the exchange) -- for jobs without
+// sent (its latency then overlaps the exchange; streamed engines read its
+// weights from L2 meanwhile) -- for jobs without
 // MidState (vanilla, budget leaves, checkpoint passes); a third delta buffer
 // keeps the re-scanned rows intact while the other CTAs already write the
 // next tick's delta, and the MidState buffers are left out.
@@ -249,7 +250,9 @@ struct DenseCfg {
   // chunks (measured: 8 rows for 4-CTA clusters, 16 for 8-CTA ones) trade
   // a little loop work for a shorter re-scan
   static constexpr int CH = STREAM ? (KPM <= 512 ? 8 : 16) : C;
-  static constexpr int NST = KPM <= 512 ? 8 : 5;  // streamed: ring stages of 4 rows per warp
+  // streamed: ring stages of 4 rows per warp (4 when the third delta
+  // buffer of a deferred K <= 1024 configuration takes the room of one)
+  static constexpr int NST = KPM <= 512 ? 8 : (DEFER ? 4 : 5);
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
   static constexpr int NDB = DEFER ? 3 : 2;   // delta buffers
   static constexpr int NMID = DEFER ? 0 : 2;  // MidState buffers
@@ -277,7 +280,7 @@ template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW, bool DEFER
 __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
   constexpr int NDB = Cfg::NDB;
-  static_assert(!DEFER || (!STREAM && CL > 1), "deferred re-scan: resident multi-CTA configurations");
+  static_assert(!DEFER || CL > 1, "deferred re-scan: multi-CTA configurations");
   constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT, KP = Cfg::KP, C = Cfg::C, KPS = Cfg::KPS;
   constexpr int CG = Cfg::CG, RG = Cfg::RG, WC = Cfg::WC;
   constexpr int CH = Cfg::CH, NST = Cfg::NST;
@@ -690,6 +693,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
             fadd2_max3(acc[x][2 * g + 1], dq[x].y, aq[1][g].y);
           }
         if ((it + 1) % (CH / 4) == 0) {
+          // acc is the running maximum over the rows so far: a chunk that
+          // raised it holds the first row reaching the new maximum
           const int c = rg * (C / CH) + it / (CH / 4);
 #pragma unroll
           for (int x = 0; x < 4; ++x)
@@ -940,6 +945,44 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
         }
       }
     };
+    // streamed deferred configurations: the winning chunks' weights go into
+    // this warp's ring slice (idle until the next tick's first copies; each
+    // lane reads back only what it staged) with cp.async right after the
+    // merge, so their L2 latency overlaps + E and the exchange
+    static_assert(!(STREAM && DEFER) || OPT * CH * 32 <= NST * 4 * WC, "re-scan staging fits the warp's ring");
+    auto stage_issue = [&]() {
+      if constexpr (STREAM && DEFER) {
+        float4* stg = reinterpret_cast<float4*>(ring);
+        const float* colp = a.wide_AT + (int64_t)(jcol < K ? jcol : 0) * wide_lane_stride(K);
+#pragma unroll
+        for (int r = 0; r < OPT; ++r)
+#pragma unroll
+          for (int k = 0; k < CH / 4; ++k) cp_async16(stg + (r * (CH / 4) + k) * 32 + lane, colp + wbase[r] + 4 * k);
+        cp_async_commit();
+      }
+    };
+    auto stage_finish = [&]() {
+      if constexpr (STREAM && DEFER) {
+        cp_async_wait<0>();
+        const float4* stg = reinterpret_cast<const float4*>(ring);
+#pragma unroll
+        for (int r = 0; r < OPT; ++r) {
+          const int s = s0 + r * SSTEP;
+          const float* dr = sD + (cur * S + s) * KPS + wbase[r] + ((wbase[r] >> 5) << 2);
+#pragma unroll
+          for (int k = CH / 2 - 1; k >= 0; --k) {
+            const float4 q = stg[(r * (CH / 4) + k / 2) * 32 + lane];
+            const float lo = (k & 1) ? q.z : q.x, hi = (k & 1) ? q.w : q.y;
+            const unsigned long long av =
+                ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
+            float c0, c1;
+            fadd2(*reinterpret_cast<const unsigned long long*>(dr + 2 * k), av, c0, c1);
+            if (c1 == best[r]) { arg[r] = wbase[r] + 2 * k + 1; val[r] = c1; }
+            if (c0 == best[r]) { arg[r] = wbase[r] + 2 * k; val[r] = c0; }
+          }
+        }
+      }
+    };
     bool rescanned = false;
     if constexpr (DEFER) {
       bool zero = false;
@@ -948,6 +991,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       if (zero) {
         rescan();
         rescanned = true;
+      } else {
+        stage_issue();
       }
     } else {
       rescan();
@@ -1093,14 +1138,22 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       __syncthreads();
     }
     if constexpr (DEFER) {
-      // the deferred re-scan (delta_t is on its way to the other CTAs)
+      // the deferred re-scan (delta_t is on its way to the other CTAs);
+      // staged copies are always waited for before the ring is reused
       uint32_t psi_bits = 0;
 #pragma unroll
       for (int r = 0; r < OPT; ++r) psi_bits |= st_mask & (1u << (2 * r));
-      if (psi_bits && !rescanned) rescan();
+      if (!rescanned) {
+        if constexpr (STREAM) {
+          stage_finish();
+        } else {
+          if (psi_bits) rescan();
+        }
+      }
 #pragma unroll
       for (int r = 0; r < OPT; ++r)
         if (st_mask & (1u << (2 * r))) st_arg[r] = arg[r] < K ? arg[r] : 0;
+      if constexpr (STREAM) __syncwarp();
     }
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
@@ -1404,9 +1457,9 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
   }
   // jobs without MidState (exact decoding with psi rows, budget leaves,
-  // checkpoint passes) on the resident 8-CTA configuration defer the
-  // re-scan past the delta exchange (measured: 8% less time at K=512; with
-  // the 2-CTA cluster barrier of K <= 256 it was 1-2% slower, not used)
+  // checkpoint passes) on the 8-CTA configurations defer the re-scan past
+  // the delta exchange (measured: 8% less time at K=512; with the 2-CTA
+  // cluster barrier of K <= 256 it was 1-2% slower, not used)
   const bool defer = a.kind == kJobVanilla || a.kind == kJobLeaf || (a.kind == kJobRoot && a.ckpt);
   if (a.K <= 256) {
     if (v == 2) return launch_dense_cfg<128, 8, 16, 2, 256, false, 8>(a, max_clusters, st);
@@ -1423,7 +1476,11 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     if (defer) return launch_dense_cfg<64, 8, 16, 8, 512, false, 4, true>(a, max_clusters, st);
     return launch_dense_cfg<64, 8, 16, 8, 512, false, 4>(a, max_clusters, st);
   }
-  if (v == 1) return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4>(a, max_clusters, st);
+  if (v == 1) {
+    if (defer) return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4, true>(a, max_clusters, st);
+    return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4>(a, max_clusters, st);
+  }
+  if (defer) return launch_dense_cfg<128, 8, 8, 8, 1024, true, 8, true>(a, max_clusters, st);
   return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);
 }
 
