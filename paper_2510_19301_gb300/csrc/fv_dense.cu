@@ -460,8 +460,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
     float2* ring = STREAM ? reinterpret_cast<float2*>(sA) + warp * NST * 2 * WC : nullptr;
     const float2* gsrc = STREAM ? a.Ap + (int64_t)(rg * C / 2) * a.ap_stride + j0 + cg * WC : nullptr;
     constexpr int NIT = C / 4;
-    auto issue = [&](int it) {
-      float2* dst = ring + (it % NST) * 2 * WC;
+    auto issue = [&](int it, int slot) {
+      float2* dst = ring + slot * 2 * WC;
 #pragma unroll
       for (int u = 0; u < WC / 32; ++u) {
         const int q = lane + 32 * u, pr = q / (WC / 2), c2 = (q % (WC / 2)) * 2;
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
     if constexpr (STREAM) {
 #pragma unroll
       for (int k = 0; k < NST - 1; ++k) {
-        if (k < NIT) issue(k);
+        if (k < NIT) issue(k, k);
         cp_async_commit();
       }
     }
@@ -666,44 +666,48 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
       const int i0 = rg * C;
       const float* dbase0 = sD + (cur * S + sg * 4) * KPS;
 #pragma unroll 1
-      for (int it = 0; it < NIT; ++it) {
-        cp_async_wait<NST - 2>();
-        __syncwarp();
-        if (it + NST - 1 < NIT) issue(it + NST - 1);
-        cp_async_commit();
-        const int i = i0 + 4 * it;
-        const float* dbase = dbase0 + i + ((i >> 5) << 2);
-        const float2* abase = ring + (it % NST) * 2 * WC + 2 * jg;
-        ulonglong2 dq[4];
+      for (int it0 = 0; it0 < NIT; it0 += CH / 4) {
+        // one chunk (CH rows) per pass, unrolled: the ring slot is a
+        // compile-time index when the ring has one stage per 4-row step
 #pragma unroll
-        for (int x = 0; x < 4; ++x) dq[x] = *reinterpret_cast<const ulonglong2*>(dbase + x * KPS);
-        ulonglong2 aq[2][TW / 2];
+        for (int u = 0; u < CH / 4; ++u) {
+          const int it = it0 + u;
+          cp_async_wait<NST - 2>();
+          __syncwarp();
+          if (it + NST - 1 < NIT) issue(it + NST - 1, NST == CH / 4 ? (u + NST - 1) % NST : (it + NST - 1) % NST);
+          cp_async_commit();
+          const int i = i0 + 4 * it;
+          const float* dbase = dbase0 + i + ((i >> 5) << 2);
+          const float2* abase = ring + (NST == CH / 4 ? u : it % NST) * 2 * WC + 2 * jg;
+          ulonglong2 dq[4];
 #pragma unroll
-        for (int pr = 0; pr < 2; ++pr)
+          for (int x = 0; x < 4; ++x) dq[x] = *reinterpret_cast<const ulonglong2*>(dbase + x * KPS);
+          ulonglong2 aq[2][TW / 2];
 #pragma unroll
-          for (int g = 0; g < TW / 2; ++g)
-            aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + pr * WC + 2 * LJ * g);
+          for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int g = 0; g < TW / 2; ++g) {
-            fadd2_max3(acc[x][2 * g], dq[x].x, aq[0][g].x);
-            fadd2_max3(acc[x][2 * g], dq[x].y, aq[1][g].x);
-            fadd2_max3(acc[x][2 * g + 1], dq[x].x, aq[0][g].y);
-            fadd2_max3(acc[x][2 * g + 1], dq[x].y, aq[1][g].y);
-          }
-        if ((it + 1) % (CH / 4) == 0) {
-          // acc is the running maximum over the rows so far: a chunk that
-          // raised it holds the first row reaching the new maximum
-          const int c = rg * (C / CH) + it / (CH / 4);
+            for (int g = 0; g < TW / 2; ++g)
+              aq[pr][g] = *reinterpret_cast<const ulonglong2*>(abase + pr * WC + 2 * LJ * g);
 #pragma unroll
           for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < TW; ++y) {
-              if (acc[x][y] > bst[x][y]) { bst[x][y] = acc[x][y]; bch[x][y] = c; }
-              acc[x][y] = -CUDART_INF_F;
+            for (int g = 0; g < TW / 2; ++g) {
+              fadd2_max3(acc[x][2 * g], dq[x].x, aq[0][g].x);
+              fadd2_max3(acc[x][2 * g], dq[x].y, aq[1][g].x);
+              fadd2_max3(acc[x][2 * g + 1], dq[x].x, aq[0][g].y);
+              fadd2_max3(acc[x][2 * g + 1], dq[x].y, aq[1][g].y);
             }
         }
+        // acc is the running maximum over the rows so far: a chunk that
+        // raised it holds the first row reaching the new maximum
+        const int c = rg * (C / CH) + it0 / (CH / 4);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < TW; ++y) {
+            if (acc[x][y] > bst[x][y]) bch[x][y] = c;
+            bst[x][y] = acc[x][y];
+          }
       }
       cp_async_wait<0>();
 #pragma unroll

@@ -532,7 +532,8 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
           }
         const int lr0 = warp * RPW;
         const float* dlanes = sD + (sg * 4) * RPCS;
-        auto quad = [&](int lr, const float2* abase) {
+        // 4 rows x (4 lanes x 8 targets); no chunk bookkeeping
+        auto quad_math = [&](int lr, const float2* abase) {
           const float* dbase = dlanes + lr + ((lr >> 5) << 2);
           ulonglong2 dq[4];
 #pragma unroll
@@ -552,29 +553,50 @@ __global__ void __launch_bounds__(kWNT, 1) wide_fwd_kernel(DenseArgs a, WideGeom
               wfadd2_max3(acc[x][2 * gq + 1], dq[x].x, aq[0][gq].y);
               wfadd2_max3(acc[x][2 * gq + 1], dq[x].y, aq[1][gq].y);
             }
-          if (((lr + 4) & (kWCH - 1)) == 0) {
-            const int c = lr / kWCH;
+        };
+        // end of chunk c: acc is the running maximum over the rows so far,
+        // so a chunk that raised it holds the first row reaching the new
+        // maximum
+        auto track = [&](int c) {
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+          for (int x = 0; x < 4; ++x)
 #pragma unroll
-              for (int y = 0; y < 8; ++y) {
-                if (acc[x][y] > bst[x][y]) { bst[x][y] = acc[x][y]; bch[x][y] = c; }
-                acc[x][y] = -CUDART_INF_F;
-              }
-          }
+            for (int y = 0; y < 8; ++y) {
+              if (acc[x][y] > bst[x][y]) bch[x][y] = c;
+              bst[x][y] = acc[x][y];
+            }
+        };
+        auto quad = [&](int lr, const float2* abase) {
+          quad_math(lr, abase);
+          if (((lr + 4) & (kWCH - 1)) == 0) track(lr / kWCH);
         };
         const float2* aw = sA + (size_t)warp * (RWR / 2) * kWJ + 2 * jg;
 #pragma unroll 1
         for (int q = 0; q < RWR / 4; ++q) quad(lr0 + 4 * q, aw + (2 * q) * kWJ);
         if (!ring_ready) prefetch_ring();  // else issued during the previous step's tail
         ring_ready = false;
-#pragma unroll 1
-        for (int it = 0; it < NIT; ++it) {
+        auto stream_math = [&](int it) {
           cp_async_wait<kWNST - 2>();
           __syncwarp();
           if (it + kWNST - 1 < NIT) issue(it + kWNST - 1);
           cp_async_commit();
-          quad(lr0 + RWR + 4 * it, ring + (it % kWNST) * 2 * kWJ + 2 * jg);
+          quad_math(lr0 + RWR + 4 * it, ring + (it % kWNST) * 2 * kWJ + 2 * jg);
+        };
+        // streamed rows up to the first chunk boundary (the resident rows
+        // end on a multiple of 4, not of kWCH), then whole chunks unrolled
+        // (RPW is a multiple of kWCH, so no partial chunk is left)
+        int it = 0;
+#pragma unroll 1
+        for (; it < NIT && ((RWR + 4 * it) & (kWCH - 1)) != 0; ++it) {
+          stream_math(it);
+          const int lr = lr0 + RWR + 4 * it;
+          if (((lr + 4) & (kWCH - 1)) == 0) track(lr / kWCH);
+        }
+#pragma unroll 1
+        for (; it < NIT; it += kWCH / 4) {
+#pragma unroll
+          for (int u = 0; u < kWCH / 4; ++u) stream_math(it + u);
+          track((lr0 + RWR + 4 * it) / kWCH);
         }
         cp_async_wait<0>();
         __syncwarp();
