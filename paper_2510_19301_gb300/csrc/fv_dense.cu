@@ -234,7 +234,10 @@ constexpr long long kClusterWaitCycles = 1ll << 31;
 // MidState (vanilla, budget leaves, checkpoint passes); a third delta buffer
 // keeps the re-scanned rows intact while the other CTAs already write the
 // next tick's delta, and the MidState buffers are left out.
-template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, bool DEFER = false>
+// MINB: CTAs per SM the configuration is sized for (2: the slab, the
+// buffers and the registers of two CTAs fit one SM, so two independent
+// clusters overlap one's max-plus loop with the other's merge and exchange)
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, bool DEFER = false, int MINB = 1>
 struct DenseCfg {
   static constexpr int NT = NW * 32;
   static constexpr int LS = S / 4;        // slot groups per warp
@@ -269,16 +272,16 @@ struct DenseCfg {
   // workspace, one row of KP floats per slot of each cluster)
   static constexpr bool GSNAP =
       STREAM || (a_floats + (size_t)NDB * S * KPS + (size_t)RG * S * J + (size_t)S * KP) * sizeof(float) +
-                        (size_t)NMID * S * KP * sizeof(uint16_t) > (size_t)220 * 1024;
+                        (size_t)NMID * S * KP * sizeof(uint16_t) > (size_t)(MINB >= 2 ? 100 : 220) * 1024;
   static constexpr size_t snap_floats = GSNAP ? 0 : (size_t)S * KP;
   static constexpr size_t smem_bytes =
       sizeof(float) * (a_floats + (size_t)NDB * S * KPS + (size_t)RG * S * J + snap_floats) +
       sizeof(uint16_t) * (size_t)NMID * S * KP + (STREAM ? (size_t)RG * S * J : 0);
 };
 
-template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW, bool DEFER>
-__global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW, bool DEFER, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) dense_fwd_kernel(DenseArgs a) {
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER, MINB>;
   constexpr int NDB = Cfg::NDB;
   static_assert(!DEFER || CL > 1, "deferred re-scan: multi-CTA configurations");
   constexpr int NT = Cfg::NT, LJ = Cfg::LJ, OPT = Cfg::OPT, KP = Cfg::KP, C = Cfg::C, KPS = Cfg::KPS;
@@ -290,8 +293,8 @@ __global__ void __launch_bounds__(NW * 32, 1) dense_fwd_kernel(DenseArgs a) {
   __shared__ SlotFin s_fin[S];
   __shared__ TickDesc tdesc[S];
   static_assert(Cfg::smem_bytes + (sizeof(Slot) + 2 * sizeof(PJob) + sizeof(SlotFin) + sizeof(TickDesc)) * S + 64 <=
-                    227 * 1024,
-                "dynamic + static shared memory within the 227 KB a CTA may use");
+                    (MINB >= 2 ? 110 : 227) * 1024,
+                "dynamic + static shared memory within what MINB CTAs per SM may use");
   // multi-CTA clusters: barrier b completes when delta_t (t & 1 == b) of
   // every CTA is in this CTA's shared memory (local warps arrive, the other
   // CTAs' 16-byte stores complete transaction bytes)
@@ -1279,10 +1282,10 @@ __global__ void path_score_kernel(ScoreArgs a, const Job* jobs, const int32_t* o
 }
 
 // ------------------------------------------------------------ host launchers
-template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, bool DEFER = false>
+template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, bool DEFER = false, int MINB = 1>
 static cudaError_t launch_dense_cfg(DenseArgs a, int max_clusters, cudaStream_t st) {
-  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW, DEFER>;
+  using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, DEFER, MINB>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW, DEFER, MINB>;
   a.KP = KPM;
   const size_t smem = Cfg::smem_bytes;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1337,7 +1340,7 @@ static int dense_cfg_slots() {
   static int cached = -1;
   if (cached >= 0) return cached;
   using Cfg = DenseCfg<J, S, NW, CL, KPM, STREAM, TW, false>;
-  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW, false>;
+  auto kern = dense_fwd_kernel<J, S, NW, CL, KPM, STREAM, TW, false, 1>;
   int dev = 0, nsm = 0, resident = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes) != cudaSuccess) {
@@ -1433,7 +1436,7 @@ int dense_variants(int K) {
   switch (dense_k_class(K)) {
     case 0: return 3;
     case 1: return 2;
-    case 2: return 3;
+    case 2: return 4;
     case 3: return 3;
     case 4: return 2;
     default: return 1;
@@ -1466,6 +1469,11 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
   // cluster barrier of K <= 256 it was 1-2% slower, not used)
   const bool defer = a.kind == kJobVanilla || a.kind == kJobLeaf || (a.kind == kJobRoot && a.ckpt);
   if (a.K <= 256) {
+    // variant 3: 4-CTA clusters of 64 columns, two CTAs per SM
+    if (v == 3) {
+      if (defer) return launch_dense_cfg<64, 8, 8, 4, 256, false, 4, true, 2>(a, max_clusters, st);
+      return launch_dense_cfg<64, 8, 8, 4, 256, false, 4, false, 2>(a, max_clusters, st);
+    }
     if (v == 2) return launch_dense_cfg<128, 8, 16, 2, 256, false, 8>(a, max_clusters, st);
     if (v == 1) return launch_dense_cfg<128, 8, 8, 2, 256, false>(a, max_clusters, st);
     return launch_dense_cfg<128, 8, 16, 2, 256, false, 4>(a, max_clusters, st);

@@ -38,7 +38,9 @@ def test_every_variant_matches_oracle(fv, K):
     try:
         for v in range(nv):
             fv.set_engine_variant(K, v)
-            for mode, kw in (("vanilla", {}), ("flash", {"P": 4})):
+            # vanilla and budget leaves take the deferred re-scan where a
+            # configuration has it; FLASH root and sub jobs do not
+            for mode, kw in (("vanilla", {}), ("flash", {"P": 4}), ("flash", {"P": 4, "mem_budget": 40 * K * 2})):
                 paths, scores = fv.decode([m], b, mode=mode, **kw)
                 paths, scores = paths.cpu().numpy(), scores.cpu().numpy()
                 off = 0
