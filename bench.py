@@ -33,11 +33,12 @@ UNIT = "state-steps/s"
 WORKLOAD = "batched-uneven: 1024 seqs, K=256 dense FP32, T~U[500,4000], E=log_softmax(N(0,1))"
 
 
-# DRAM bytes per state-step of dense_fwd_kernel (K=256, vanilla, the 16-warp
-# x 8-column configuration the autotuner picks on this batch): reads of E
-# plus writes of psi, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of a 128-sequence launch of this workload.
-DRAM_BYTES_PER_STATE_STEP = (278595072 + 109117696) / (271316 * 256)
+# DRAM bytes per state-step of dense_fwd_kernel (K=256, vanilla, the default
+# configuration: 4-CTA clusters, two CTAs per SM): reads of E plus writes of
+# psi, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
+# of a 608-sequence launch of this workload (sum of T = 1 391 599).
+DRAM_BYTES_PER_STATE_STEP = (1427830784 + 683246592) / (1391599 * 256)
+TRAFFIC_VARIANT = 0  # the configuration those counters were taken on
 
 
 def dist_env():
@@ -882,10 +883,12 @@ def run_ours(args):
            "roofline": {"bound": "alu", "kernel": "dense_fwd_kernel", "achieved": achieved,
                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "traffic": (DRAM_BYTES_PER_STATE_STEP * state_steps
-                                    if (args.K == 256 and args.mode == "vanilla") else None),
+                                    if (args.K == 256 and args.mode == "vanilla" and int(chosen[0]) == TRAFFIC_VARIANT)
+                                    else None),
                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of "
-                                        "this kernel on 128 sequences (5.61 B per state-step), scaled to this "
-                                        "launch's state-steps",
+                                        "this kernel (default configuration) on 608 sequences (%.2f B per "
+                                        "state-step), scaled to this launch's state-steps; null for another "
+                                        "configuration" % DRAM_BYTES_PER_STATE_STEP,
                         "peak_kind": "measured: fv_maxplus_peak, the engines' add + 3-input max cell on every SM "
                                      "(%.1f cells/clk/SM, 2 ops per cell)" % alu_probe["cells_per_clk_per_sm"],
                         "sm_count": sms,
