@@ -255,7 +255,9 @@ struct DenseCfg {
   static constexpr int CH = STREAM ? (KPM <= 512 ? 8 : 16) : C;
   // streamed: ring stages of 4 rows per warp (4 when the third delta
   // buffer of a deferred K <= 1024 configuration takes the room of one)
-  static constexpr int NST = KPM <= 512 ? 8 : (DEFER ? 4 : 5);
+  // (2 stages when two 8-warp CTAs share an SM: the other warps hide the
+  // shallower ring's latency)
+  static constexpr int NST = MINB >= 2 && NW >= 8 ? 2 : (KPM <= 512 ? 8 : (DEFER ? 4 : 5));
   static constexpr int KPS = KPM + KPM / 8;  // skewed delta row: i -> i + 4*(i/32)
   static constexpr int NDB = DEFER ? 3 : 2;   // delta buffers
   static constexpr int NMID = DEFER ? 0 : 2;  // MidState buffers
@@ -1375,7 +1377,7 @@ int dense_job_slots(int K) {
   if (K <= 128) return dense_cfg_slots<128, 8, 16, 1, 128, false, 4>();
   if (K <= 256) return dense_cfg_slots<64, 8, 8, 4, 256, false, 4, 2>();
   if (K <= 512) return dense_cfg_slots<64, 8, 16, 8, 512, false, 4>();
-  return dense_cfg_slots<128, 4, 4, 8, 1024, true, 4, 2>();
+  return dense_cfg_slots<128, 4, 8, 8, 1024, true, 4, 2>();
 }
 
 int dense_supported_K(int K) {
@@ -1438,7 +1440,7 @@ int dense_variants(int K) {
     case 1: return 2;
     case 2: return 4;
     case 3: return 3;
-    case 4: return 3;
+    case 4: return 4;
     default: return 1;
   }
 }
@@ -1487,6 +1489,10 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     if (defer) return launch_dense_cfg<64, 8, 16, 8, 512, false, 4, true>(a, max_clusters, st);
     return launch_dense_cfg<64, 8, 16, 8, 512, false, 4>(a, max_clusters, st);
   }
+  if (v == 3) {
+    if (defer) return launch_dense_cfg<128, 4, 4, 8, 1024, true, 4, true, 2>(a, max_clusters, st);
+    return launch_dense_cfg<128, 4, 4, 8, 1024, true, 4, false, 2>(a, max_clusters, st);
+  }
   if (v == 2) {
     if (defer) return launch_dense_cfg<128, 8, 8, 8, 1024, true, 8, true>(a, max_clusters, st);
     return launch_dense_cfg<128, 8, 8, 8, 1024, true>(a, max_clusters, st);
@@ -1495,11 +1501,12 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     if (defer) return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4, true>(a, max_clusters, st);
     return launch_dense_cfg<128, 8, 16, 8, 1024, true, 4>(a, max_clusters, st);
   }
-  // default: 4 slots and 4 warps per CTA, two CTAs per SM (the same 152
-  // slots as 8 slots on one CTA per SM; measured 12% less time on 256
-  // sequences)
-  if (defer) return launch_dense_cfg<128, 4, 4, 8, 1024, true, 4, true, 2>(a, max_clusters, st);
-  return launch_dense_cfg<128, 4, 4, 8, 1024, true, 4, false, 2>(a, max_clusters, st);
+  // default: 4 slots and 8 warps per CTA, a 2-stage ring, two CTAs per SM
+  // (about the slot count of 8 slots on one CTA per SM; measured on 256
+  // sequences: 67 ms, against 73 ms with 4 warps and a 4-stage ring and 83
+  // ms for one 8-slot CTA per SM)
+  if (defer) return launch_dense_cfg<128, 4, 8, 8, 1024, true, 4, true, 2>(a, max_clusters, st);
+  return launch_dense_cfg<128, 4, 8, 8, 1024, true, 4, false, 2>(a, max_clusters, st);
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t st) {

@@ -15,12 +15,12 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("K,variant", [(1100, 0), (300, 0), (300, 1), (1000, 0), (1000, 2), (200, 0)])
+@pytest.mark.parametrize("K,variant", [(1100, 0), (300, 0), (300, 1), (1000, 0), (1000, 2), (1000, 3), (200, 0)])
 def test_withheld_step_times_out_and_context_survives(K, variant):
     """K=300: variant 0 is the resident 8-CTA cluster configuration of the
-    K <= 512 class, variant 1 the streamed 4-CTA one; K=1000 variant 0 and
-    K=200 variant 0 run two CTAs per SM, K=1000 variant 2 one 8-warp CTA;
-    all exchange delta through mbarriers."""
+    K <= 512 class, variant 1 the streamed 4-CTA one; K=1000 variants 0
+    and 3 and K=200 variant 0 run two CTAs per SM, K=1000 variant 2 one
+    8-warp CTA; all exchange delta through mbarriers."""
     import paper_2510_19301_gb300 as fv
     from paper_2510_19301_gb300 import _lib as L
     fv._lib.load(build_if_missing=True)
