@@ -1373,7 +1373,7 @@ static int dense_cfg_slots() {
 
 int dense_job_slots(int K) {
   if (K > 1024) return kWideLanes;
-  if (K <= 64) return dense_cfg_slots<64, 16, 4, 1, 64, false>();
+  if (K <= 64) return dense_cfg_slots<64, 16, 16, 1, 64, false, 4>();
   if (K <= 128) return dense_cfg_slots<128, 8, 16, 1, 128, false, 4>();
   if (K <= 256) return dense_cfg_slots<64, 8, 8, 4, 256, false, 4, 2>();
   if (K <= 512) return dense_cfg_slots<64, 8, 16, 8, 512, false, 4>();
@@ -1436,8 +1436,8 @@ int dense_k_class(int K) {
 }
 int dense_variants(int K) {
   switch (dense_k_class(K)) {
-    case 0: return 3;
-    case 1: return 2;
+    case 0: return 4;
+    case 1: return 3;
     case 2: return 4;
     case 3: return 3;
     case 4: return 4;
@@ -1459,10 +1459,19 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
   if (a.K <= 64) {
     if (v == 1) return launch_dense_cfg<64, 16, 8, 1, 64, false, 4>(a, max_clusters, st);
     if (v == 2) return launch_dense_cfg<64, 16, 16, 1, 64, false, 4>(a, max_clusters, st);
-    return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
+    if (v == 3) return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
+    // default: exact jobs on the one-CTA-per-sequence small-K kernel
+    // (fv_small.cu; measured 3.4x faster on one K=64 sequence and 3.3x on
+    // 1024), other job kinds on 16 warps x 4 columns
+    if (a.kind == kJobVanilla) return launch_small_forward(a, st);
+    return launch_dense_cfg<64, 16, 16, 1, 64, false, 4>(a, max_clusters, st);
   }
   if (a.K <= 128) {
     if (v == 1) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
+    if (v == 2) return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
+    // default: exact jobs on the small-K kernel (measured 3.9x faster on one
+    // K=128 sequence, 1.7x on 1024), other job kinds on 16 warps x 4
+    if (a.kind == kJobVanilla) return launch_small_forward(a, st);
     return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
   }
   // jobs without MidState (exact decoding with psi rows, budget leaves,

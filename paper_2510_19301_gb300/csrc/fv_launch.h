@@ -202,6 +202,8 @@ int device_sm_count();
 bool wide_geometry(int K, int nsm, WideGeom* g);
 size_t wide_scratch_bytes(int K, int nsm);
 cudaError_t launch_wide_forward(DenseArgs a, cudaStream_t st);
+// exact (vanilla) jobs with K <= 128: one CTA per sequence, a thread per state
+cudaError_t launch_small_forward(const DenseArgs& a, cudaStream_t st);
 // AT[j * KD + i] = logA[i * K + j] (rows K..KD-1 are -inf), KD = wide_lane_stride(K).
 cudaError_t launch_wide_transpose(const float* logA, int K, float* AT, cudaStream_t st);
 void dense_stream_geometry(int K, int* KPM, int* cols);
