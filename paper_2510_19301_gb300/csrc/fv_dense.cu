@@ -210,15 +210,6 @@ __device__ __forceinline__ void fadd2(unsigned long long d, unsigned long long a
   asm("mov.b64 {%0, %1}, %2;" : "=f"(c0), "=f"(c1) : "l"(c));
 }
 
-__host__ __device__ inline int32_t flash_pe(int32_t T, int32_t P) {
-  if (T <= 1) return 1;
-  int32_t p = P < 2 ? 2 : P;
-  return p < T ? p : T;
-}
-// Division point e_k = floor(((k+1)T - 1) / P') of the P-way first split.
-__host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
-  return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
-}
 
 // bounded wait of the multi-CTA exchange (~1 s at 2 GHz); on expiry the
 // engine records FV_ETIMEOUT and stops at the next tick
@@ -1335,8 +1326,11 @@ int device_sm_count() {
   return nsm;
 }
 
-// Jobs the engine runs at once for K's class (default configuration):
-// resident clusters x slots; 0 when no device is visible.
+// Jobs the engine runs at once for K's class (default configuration; for
+// K <= 128, whose default is the one-CTA-per-job small-K engine, the slot
+// engine's 16-warp configuration): resident clusters x slots; 0 when no
+// device is visible.  It sizes the waves of budget leaves, which any engine
+// runs in any order.
 template <int J, int S, int NW, int CL, int KPM, bool STREAM, int TW = 8, int MINB = 1>
 static int dense_cfg_slots() {
   static int cached = -1;
@@ -1460,19 +1454,16 @@ cudaError_t launch_dense_forward(DenseArgs a, int max_clusters, cudaStream_t st)
     if (v == 1) return launch_dense_cfg<64, 16, 8, 1, 64, false, 4>(a, max_clusters, st);
     if (v == 2) return launch_dense_cfg<64, 16, 16, 1, 64, false, 4>(a, max_clusters, st);
     if (v == 3) return launch_dense_cfg<64, 16, 4, 1, 64, false>(a, max_clusters, st);
-    // default: exact jobs on the one-CTA-per-sequence small-K kernel
-    // (fv_small.cu; measured 3.4x faster on one K=64 sequence and 3.3x on
-    // 1024), other job kinds on 16 warps x 4 columns
-    if (a.kind == kJobVanilla) return launch_small_forward(a, st);
-    return launch_dense_cfg<64, 16, 16, 1, 64, false, 4>(a, max_clusters, st);
+    // default: the one-CTA-per-job small-K engine (fv_small.cu; measured
+    // 3.4x faster on one K=64 sequence and 3.3x on 1024)
+    return launch_small_forward(a, st);
   }
   if (a.K <= 128) {
     if (v == 1) return launch_dense_cfg<128, 8, 8, 1, 128, false>(a, max_clusters, st);
     if (v == 2) return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
-    // default: exact jobs on the small-K kernel (measured 3.9x faster on one
-    // K=128 sequence, 1.7x on 1024), other job kinds on 16 warps x 4
-    if (a.kind == kJobVanilla) return launch_small_forward(a, st);
-    return launch_dense_cfg<128, 8, 16, 1, 128, false, 4>(a, max_clusters, st);
+    // default: the small-K engine (measured 3.9x faster on one K=128
+    // sequence, 1.7x on 1024)
+    return launch_small_forward(a, st);
   }
   // jobs without MidState (exact decoding with psi rows, budget leaves,
   // checkpoint passes) on the 8-CTA configurations defer the re-scan past

@@ -41,6 +41,17 @@ struct Task {
   int32_t b, m, n, pad;
 };
 
+// FLASH's first split (Sec. V-A): P' = min(max(P, 2), T) parts.
+__host__ __device__ inline int32_t flash_pe(int32_t T, int32_t P) {
+  if (T <= 1) return 1;
+  int32_t p = P < 2 ? 2 : P;
+  return p < T ? p : T;
+}
+// Division point e_k = floor(((k+1)T - 1) / P') of the P-way first split.
+__host__ __device__ inline int32_t flash_div(int32_t k, int32_t T, int32_t Pe) {
+  return (int32_t)((((int64_t)k + 1) * T - 1) / Pe);
+}
+
 // Checkpoint Viterbi (the sqrt(T)-checkpoint baseline of Sec. II-A): the
 // number C of checkpoints of a length-T sequence, ceil(sqrt(T)) unless P >= 1
 // asks for P, at most T.  Checkpoint k is delta at the division point
