@@ -1,9 +1,10 @@
-"""The small-K exact kernel (K <= 128, one CTA of 64 or 128 threads per
-sequence, the default for exact decoding at K <= 128) against the oracle: paths
-identical, scores equal to 0 ulp, on the cases that exercise the argmax
-rule (integer ties, -inf transitions and all--inf steps, signed zeros),
-discrete emissions, several models in one batch and a batch of many
-sequences."""
+"""The small-K engine (K <= 128, one CTA of 64 or 128 threads per job, the
+default at K <= 128) against the oracle: paths identical, scores equal to
+0 ulp, on the cases that exercise the argmax rule (integer ties, -inf
+transitions and all--inf steps, signed zeros), discrete emissions, several
+models in one batch, a batch of many sequences, and every job kind: FLASH
+root passes and subtasks (retained offset and complete pruning), budget
+leaves and both Checkpoint Viterbi passes."""
 import numpy as np
 import pytest
 
@@ -157,3 +158,61 @@ def test_many_sequences_up_to_128(small128):
     log_pi, logA = W.random_model(K, rng)
     lengths = [int(t) for t in rng.integers(1, 120, 1500)]
     check(small128, log_pi, logA, [W.gaussian_emissions(t, K, rng) for t in lengths])
+
+
+def decode_modes_check(fv, log_pi, logA, E_list, mode, **kw):
+    """One decode in `mode` against the oracle's restatement of it."""
+    lengths = [e.shape[0] for e in E_list]
+    m = fv.Model(log_pi, logA)
+    b = fv.Batch(lengths, E=torch.from_numpy(np.concatenate(E_list)).cuda(), models=[m])
+    complete = bool(kw.pop("complete", False))
+    flags = fv._lib.FV_COMPLETE_PRUNING if complete else 0
+    paths, scores = fv.decode([m], b, mode=mode, flags=flags, **kw)
+    paths, scores = paths.cpu().numpy(), scores.cpu().numpy()
+    hmm = oracle.HMM(log_pi, logA)
+    P = kw.get("P", 1)
+    if mode == "checkpoint":
+        ref = oracle.map_sequences(lambda e: oracle.checkpoint(hmm, e, P)[:2], E_list)
+    elif kw.get("mem_budget"):
+        rows = kw["mem_budget"] // (2 * log_pi.shape[0])
+        ref = oracle.map_sequences(lambda e: oracle.flash_budget(hmm, e, P, rows, complete=complete)[:2], E_list)
+    else:
+        ref = oracle.map_sequences(lambda e: oracle.flash(hmm, e, P, complete=complete)[:2], E_list)
+    off = 0
+    for i, (p, s) in enumerate(ref):
+        T = lengths[i]
+        assert np.array_equal(paths[off:off + T], p), f"{mode} {kw} seq {i} (T={T})"
+        if not complete:
+            assert bits(scores[i]) == bits(s), f"{mode} {kw} seq {i} score"
+        off += T
+
+
+@pytest.mark.parametrize("K", [5, 37, 64, 100, 128])
+@pytest.mark.parametrize("case", ["flash4", "flash16", "flash_complete", "budget", "checkpoint"])
+def test_flash_budget_checkpoint_kinds(fv, K, case):
+    """FLASH root passes and subtasks, budget leaves and both Checkpoint
+    Viterbi passes on the small-K engine (the K <= 128 default)."""
+    fv.set_engine_variant(K, 0)
+    rng = np.random.default_rng(1100 + K)
+    log_pi, logA = W.random_model(K, rng)
+    lengths = [1, 2, 3, 9, 40, 130, 257] + [int(t) for t in rng.integers(1, 300, 12)]
+    E_list = [W.gaussian_emissions(t, K, rng) for t in lengths]
+    kw = {"flash4": dict(mode="flash", P=4), "flash16": dict(mode="flash", P=16),
+          "flash_complete": dict(mode="flash", P=4, complete=True),
+          "budget": dict(mode="flash", P=4, mem_budget=24 * K * 2),
+          "checkpoint": dict(mode="checkpoint", P=0)}[case]
+    mode = kw.pop("mode")
+    decode_modes_check(fv, log_pi, logA, E_list, mode, **kw)
+
+
+def test_integer_ties_flash_and_budget(fv):
+    rng = np.random.default_rng(1200)
+    K = 40
+    fv.set_engine_variant(K, 0)
+    log_pi = rng.integers(-2, 3, K).astype(np.float32)
+    logA = rng.integers(-2, 3, (K, K)).astype(np.float32)
+    logA[rng.random((K, K)) < 0.6] = -np.inf
+    E_list = [rng.integers(-2, 3, (int(t), K)).astype(np.float32) for t in rng.integers(1, 120, 20)]
+    decode_modes_check(fv, log_pi, logA, E_list, "flash", P=8)
+    decode_modes_check(fv, log_pi, logA, E_list, "flash", P=8, mem_budget=16 * K * 2)
+    decode_modes_check(fv, log_pi, logA, E_list, "checkpoint", P=0)
