@@ -1,5 +1,6 @@
-// fv_small.cu -- the forward engine for small state spaces, K <= 128: one
-// CTA of KM threads (KM = 64 or 128, the class bound) per job, for every
+// fv_small.cu -- the forward engine for small state spaces, K <= 128: a
+// persistent grid of CTAs of KM threads (KM = 64 or 128, the class bound),
+// each running one job at a time from the launch's counter, for every
 // job kind of the slot engine: exact decoding with psi rows (Sec. III-A),
 // the FLASH root pass with MidState, delta snapshots and ancestor maps at
 // the division points, FLASH subtasks from the pruned start (Alg. 2,
@@ -55,192 +56,221 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
   extern __shared__ float sB_dyn[];
   if (a.hdr->status != 0) return;  // an earlier kernel recorded an error
   const int kind = VAN ? (int)kJobVanilla : a.kind, K = a.K, j = threadIdx.x;
-  // ---- this CTA's job: a sequence (exact decoding, FLASH root pass) or a
-  // task of the current list (FLASH subtask, budget or checkpoint leaf)
-  int b, m, n, pad = 0, q_prev = 0, q_n = 0, Pe = 1;
-  float s_prev = 0.f;
-  if (kind == kJobVanilla || kind == kJobRoot) {
-    if ((int)blockIdx.x >= a.order_count) return;
-    b = a.order[a.order_begin + blockIdx.x];
-    m = 0;
-    n = a.jobs[b].T - 1;
-  } else {
-    if ((int)blockIdx.x >= *a.task_count) return;
-    const Task tk = a.tasks[(a.task_first ? *a.task_first : 0) + (int64_t)blockIdx.x];
-    b = tk.b;
-    m = tk.m;
-    n = tk.n;
-    pad = tk.pad;
-  }
-  const Job jb = a.jobs[b];
-  const int T = jb.T;
-  if (T < 1 || n < m) return;
-  if (kind == kJobRoot || (kind == kJobLeaf && a.ckpt)) Pe = a.ckpt ? ckpt_count(T, a.P) : flash_pe(T, a.P);
-  if ((kind == kJobSub || kind == kJobLeaf) && !a.ckpt) {
-    // states revealed by earlier levels (clamped into [0, K))
-    const int qn = a.paths[jb.path_off + n];
-    q_n = (unsigned)qn < (unsigned)K ? qn : 0;
-    if (m > 0) {
-      const int qp = a.paths[jb.path_off + m - 1];
-      q_prev = (unsigned)qp < (unsigned)K ? qp : 0;
-      s_prev = a.sval[jb.aux_off + m - 1];
-    }
-  }
   const bool own = j < K;
-  if (!VAN) {
-    smid[0][j] = smid[1][j] = 0;
-    ssnap[j] = -CUDART_INF_F;
-  }
-  // rows and states beyond K are -inf, so they never win
+  // rows and states beyond K are -inf, so they never win; the model is the
+  // same for every job of the launch, so the column stays in registers
   float A[KM];
+  auto load_column = [&]() {
 #pragma unroll
-  for (int i = 0; i < KM; ++i) A[i] = (own && i < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
+    for (int i = 0; i < KM; ++i) A[i] = (own && i < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
+  };
+  if constexpr (!VAN) load_column();
   const float* sB = nullptr;
   if (small_stage_logB<KM>(a)) {
     for (int x = 0; x < a.V; ++x) sB_dyn[x * KM + j] = own ? __ldg(a.logB + (int64_t)j * a.V + x) : 0.f;
     sB = sB_dyn;
-    __syncthreads();
   }
-  // root pass: division points (Sec. V-A) or checkpoints
-  int kdiv = 0, ediv = kind == kJobRoot ? flash_div(0, T, Pe) : 0x7fffffff, eprev = -1;
-  const int tmid = (m + n) / 2;  // sub jobs
-  // E_{t}, ..., E_{t+kSmallAhead-1} of this state, oldest first
-  float er[kSmallAhead];
-#pragma unroll
-  for (int k = 0; k < kSmallAhead; ++k) er[k] = (own && m + k <= n) ? small_emit<KM>(a, jb, m + k, j, sB) : 0.f;
-  int cur = 0;
-  for (int t = m; t <= n; ++t) {
-    const float e = er[0];
-#pragma unroll
-    for (int k = 0; k + 1 < kSmallAhead; ++k) er[k] = er[k + 1];
-    er[kSmallAhead - 1] = (own && t + kSmallAhead <= n) ? small_emit<KM>(a, jb, t + kSmallAhead, j, sB) : 0.f;
-    float dval;
-    int g = 0;
-    uint32_t mnew = 0;
-    int f_mid = 0;
-    if (t == m) {
-      // first step of the job: pi, a stored checkpoint, or the pruned start
-      // from the revealed state q_{m-1} (Sec. V-B.2)
-      if (t == 0) {
-        dval = own ? __fadd_rn(__ldg(a.log_pi + j), e) : -CUDART_INF_F;
-      } else if (a.ckpt) {
-        dval = own ? __ldg(a.snaps + jb.aux_off + (int64_t)pad * K + j) : -CUDART_INF_F;
-      } else {
-        const float av = own ? __ldg(a.logA + (int64_t)q_prev * K + j) : -CUDART_INF_F;
-        dval = a.complete ? __fadd_rn(av, e) : __fadd_rn(__fadd_rn(s_prev, av), e);
-        if (!own) dval = -CUDART_INF_F;
-      }
+  // exact decoding: one job per CTA (grid = sequences); other kinds:
+  // persistent, jobs drawn one at a time from the launch's counter, so
+  // the column is loaded once for the many short tasks of a FLASH level
+  __shared__ int s_k;
+  const bool from_tasks = kind == kJobSub || kind == kJobLeaf;
+  const int count = from_tasks ? *a.task_count : a.order_count;
+  auto run_job = [&](const int k) {
+    // ---- the job: a sequence (exact decoding, FLASH root pass) or a task
+    // of the current list (FLASH subtask, budget or checkpoint leaf)
+    int b, m, n, pad = 0, q_prev = 0, q_n = 0, Pe = 1;
+    float s_prev = 0.f;
+    if (!from_tasks) {
+      b = a.order[a.order_begin + k];
+      m = 0;
+      n = a.jobs[b].T - 1;
     } else {
-      const float4* dv = reinterpret_cast<const float4*>(sd[cur]);
-      float bq[4];
-      int gq[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        bq[q] = -CUDART_INF_F;
-        gq[q] = q * Q;
-      }
-#pragma unroll
-      for (int i4 = 0; i4 < Q / 4; ++i4)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = q * Q + 4 * i4;
-          const float4 x = dv[i / 4];
-          float c = __fadd_rn(x.x, A[i]);
-          if (c > bq[q]) { bq[q] = c; gq[q] = i; }
-          c = __fadd_rn(x.y, A[i + 1]);
-          if (c > bq[q]) { bq[q] = c; gq[q] = i + 1; }
-          c = __fadd_rn(x.z, A[i + 2]);
-          if (c > bq[q]) { bq[q] = c; gq[q] = i + 2; }
-          c = __fadd_rn(x.w, A[i + 3]);
-          if (c > bq[q]) { bq[q] = c; gq[q] = i + 3; }
-        }
-      float bv = bq[0];
-      g = gq[0];
-#pragma unroll
-      for (int q = 1; q < 4; ++q)
-        if (bq[q] > bv) { bv = bq[q]; g = gq[q]; }
-      dval = own ? __fadd_rn(bv, e) : -CUDART_INF_F;
-      if (own && (kind == kJobVanilla || kind == kJobLeaf)) {
-        const int64_t row = kind == kJobVanilla ? jb.aux_off + (int64_t)t * K
-                            : a.ckpt        ? 2 * (jb.aux_off + (int64_t)Pe * K) + (int64_t)(t - m - 1) * K
-                                            : (int64_t)(pad + t - m - 1) * K;
-        a.psi[row + j] = (uint16_t)g;
-      }
-      // MidState (Alg. 2): the argmax at the step after a division point,
-      // then carried along the argmax
-      if (kind == kJobRoot && !a.ckpt && eprev >= 0) f_mid = (t == eprev + 1) ? 1 : 2;
-      if (kind == kJobSub) f_mid = (t == tmid + 1) ? 1 : (t > tmid + 1 ? 2 : 0);
-      if (f_mid) mnew = f_mid == 1 ? (uint32_t)g : smid[cur][g];
-      // sub jobs keep delta_{tmid} (the previous step's delta)
-      if (kind == kJobSub && t == tmid + 1) ssnap[j] = sd[cur][j];
+      const Task tk = a.tasks[(a.task_first ? *a.task_first : 0) + (int64_t)k];
+      b = tk.b;
+      m = tk.m;
+      n = tk.n;
+      pad = tk.pad;
     }
-    if (f_mid) smid[cur ^ 1][j] = (uint16_t)mnew;
-    if (kind == kJobRoot && t == ediv) {
-      // division point: delta snapshot and, from the second one on, the
-      // ancestor map (MidState); checkpoints keep delta only
-      if (own) {
-        if (a.ckpt) {
-          a.snaps[jb.aux_off + (int64_t)kdiv * K + j] = dval;
+    const Job jb = a.jobs[b];
+    const int T = jb.T;
+    if (T < 1 || n < m) return;
+    if constexpr (VAN) load_column();  // (one job per CTA)
+    if (kind == kJobRoot || (kind == kJobLeaf && a.ckpt)) Pe = a.ckpt ? ckpt_count(T, a.P) : flash_pe(T, a.P);
+    if (from_tasks && !a.ckpt) {
+      // states revealed by earlier levels (clamped into [0, K))
+      const int qn = a.paths[jb.path_off + n];
+      q_n = (unsigned)qn < (unsigned)K ? qn : 0;
+      if (m > 0) {
+        const int qp = a.paths[jb.path_off + m - 1];
+        q_prev = (unsigned)qp < (unsigned)K ? qp : 0;
+        s_prev = a.sval[jb.aux_off + m - 1];
+      }
+    }
+    if (!VAN) {
+      smid[0][j] = smid[1][j] = 0;
+      ssnap[j] = -CUDART_INF_F;
+    }
+    // root pass: division points (Sec. V-A) or checkpoints
+    int kdiv = 0, ediv = kind == kJobRoot ? flash_div(0, T, Pe) : 0x7fffffff, eprev = -1;
+    const int tmid = (m + n) / 2;  // sub jobs
+    // E_{t}, ..., E_{t+kSmallAhead-1} of this state, oldest first
+    float er[kSmallAhead];
+  #pragma unroll
+    for (int k = 0; k < kSmallAhead; ++k) er[k] = (own && m + k <= n) ? small_emit<KM>(a, jb, m + k, j, sB) : 0.f;
+    int cur = 0;
+    for (int t = m; t <= n; ++t) {
+      const float e = er[0];
+  #pragma unroll
+      for (int k = 0; k + 1 < kSmallAhead; ++k) er[k] = er[k + 1];
+      er[kSmallAhead - 1] = (own && t + kSmallAhead <= n) ? small_emit<KM>(a, jb, t + kSmallAhead, j, sB) : 0.f;
+      float dval;
+      int g = 0;
+      uint32_t mnew = 0;
+      int f_mid = 0;
+      if (t == m) {
+        // first step of the job: pi, a stored checkpoint, or the pruned start
+        // from the revealed state q_{m-1} (Sec. V-B.2)
+        if (t == 0) {
+          dval = own ? __fadd_rn(__ldg(a.log_pi + j), e) : -CUDART_INF_F;
+        } else if (a.ckpt) {
+          dval = own ? __ldg(a.snaps + jb.aux_off + (int64_t)pad * K + j) : -CUDART_INF_F;
         } else {
-          a.snaps[(int64_t)b * a.snap_stride + (int64_t)kdiv * K + j] = dval;
-          if (kdiv >= 1) a.maps[(int64_t)b * a.map_stride + (int64_t)(kdiv - 1) * K + j] = (uint16_t)mnew;
+          const float av = own ? __ldg(a.logA + (int64_t)q_prev * K + j) : -CUDART_INF_F;
+          dval = a.complete ? __fadd_rn(av, e) : __fadd_rn(__fadd_rn(s_prev, av), e);
+          if (!own) dval = -CUDART_INF_F;
         }
+      } else {
+        const float4* dv = reinterpret_cast<const float4*>(sd[cur]);
+        float bq[4];
+        int gq[4];
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          bq[q] = -CUDART_INF_F;
+          gq[q] = q * Q;
+        }
+  #pragma unroll
+        for (int i4 = 0; i4 < Q / 4; ++i4)
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = q * Q + 4 * i4;
+            const float4 x = dv[i / 4];
+            float c = __fadd_rn(x.x, A[i]);
+            if (c > bq[q]) { bq[q] = c; gq[q] = i; }
+            c = __fadd_rn(x.y, A[i + 1]);
+            if (c > bq[q]) { bq[q] = c; gq[q] = i + 1; }
+            c = __fadd_rn(x.z, A[i + 2]);
+            if (c > bq[q]) { bq[q] = c; gq[q] = i + 2; }
+            c = __fadd_rn(x.w, A[i + 3]);
+            if (c > bq[q]) { bq[q] = c; gq[q] = i + 3; }
+          }
+        float bv = bq[0];
+        g = gq[0];
+  #pragma unroll
+        for (int q = 1; q < 4; ++q)
+          if (bq[q] > bv) { bv = bq[q]; g = gq[q]; }
+        dval = own ? __fadd_rn(bv, e) : -CUDART_INF_F;
+        if (own && (kind == kJobVanilla || kind == kJobLeaf)) {
+          const int64_t row = kind == kJobVanilla ? jb.aux_off + (int64_t)t * K
+                              : a.ckpt        ? 2 * (jb.aux_off + (int64_t)Pe * K) + (int64_t)(t - m - 1) * K
+                                              : (int64_t)(pad + t - m - 1) * K;
+          a.psi[row + j] = (uint16_t)g;
+        }
+        // MidState (Alg. 2): the argmax at the step after a division point,
+        // then carried along the argmax
+        if (kind == kJobRoot && !a.ckpt && eprev >= 0) f_mid = (t == eprev + 1) ? 1 : 2;
+        if (kind == kJobSub) f_mid = (t == tmid + 1) ? 1 : (t > tmid + 1 ? 2 : 0);
+        if (f_mid) mnew = f_mid == 1 ? (uint32_t)g : smid[cur][g];
+        // sub jobs keep delta_{tmid} (the previous step's delta)
+        if (kind == kJobSub && t == tmid + 1) ssnap[j] = sd[cur][j];
       }
-      eprev = ediv;
-      ++kdiv;
-      ediv = kdiv < Pe ? flash_div(kdiv, T, Pe) : 0x7fffffff;
+      if (f_mid) smid[cur ^ 1][j] = (uint16_t)mnew;
+      if (kind == kJobRoot && t == ediv) {
+        // division point: delta snapshot and, from the second one on, the
+        // ancestor map (MidState); checkpoints keep delta only
+        if (own) {
+          if (a.ckpt) {
+            a.snaps[jb.aux_off + (int64_t)kdiv * K + j] = dval;
+          } else {
+            a.snaps[(int64_t)b * a.snap_stride + (int64_t)kdiv * K + j] = dval;
+            if (kdiv >= 1) a.maps[(int64_t)b * a.map_stride + (int64_t)(kdiv - 1) * K + j] = (uint16_t)mnew;
+          }
+        }
+        eprev = ediv;
+        ++kdiv;
+        ediv = kdiv < Pe ? flash_div(kdiv, T, Pe) : 0x7fffffff;
+      }
+      sd[cur ^ 1][j] = dval;
+      __syncthreads();
+      cur ^= 1;
     }
-    sd[cur ^ 1][j] = dval;
-    __syncthreads();
-    cur ^= 1;
+    if (kind == kJobVanilla && j < 32) {
+      // termination: q_{T-1} = lowest argmax_j delta_{T-1}[j], score = delta_{T-1}[q]
+      float v = sd[cur][j];
+      int qi = j;
+  #pragma unroll
+      for (int k = 1; k < KM / 32; ++k) {
+        const float vk = sd[cur][j + 32 * k];
+        if (vk > v) { v = vk; qi = j + 32 * k; }
+      }
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, qi, o);
+        if (ov > v || (ov == v && oq < qi)) { v = ov; qi = oq; }
+      }
+      if (j == 0) {
+        a.qlast[b] = qi;
+        a.scores[b] = sd[cur][qi];
+      }
+    } else if (kind == kJobSub && j == 0) {
+      // Alg. 2 output: q*_{tmid} = MidState_n[q*_n]; its delta from the snapshot
+      int q = smid[cur][q_n];
+      q = (unsigned)q < (unsigned)K ? q : 0;
+      a.paths[jb.path_off + tmid] = q;
+      a.sval[jb.aux_off + tmid] = ssnap[q];
+    }
+  };
+  if constexpr (VAN) {
+    if (sB) __syncthreads();  // the staged table is complete
+    if ((int)blockIdx.x < count) run_job(blockIdx.x);
+  } else {
+    for (;;) {
+      if (j == 0) s_k = (int)atomicAdd(a.pop, 1ull);
+      __syncthreads();
+      const int k = s_k;
+      __syncthreads();
+      if (k >= count) break;
+      run_job(k);
+    }
   }
-  if (kind == kJobVanilla && j < 32) {
-    // termination: q_{T-1} = lowest argmax_j delta_{T-1}[j], score = delta_{T-1}[q]
-    float v = sd[cur][j];
-    int qi = j;
-#pragma unroll
-    for (int k = 1; k < KM / 32; ++k) {
-      const float vk = sd[cur][j + 32 * k];
-      if (vk > v) { v = vk; qi = j + 32 * k; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int oq = __shfl_xor_sync(0xffffffffu, qi, o);
-      if (ov > v || (ov == v && oq < qi)) { v = ov; qi = oq; }
-    }
-    if (j == 0) {
-      a.qlast[b] = qi;
-      a.scores[b] = sd[cur][qi];
-    }
-  } else if (kind == kJobSub && j == 0) {
-    // Alg. 2 output: q*_{tmid} = MidState_n[q*_n]; its delta from the snapshot
-    int q = smid[cur][q_n];
-    q = (unsigned)q < (unsigned)K ? q : 0;
-    a.paths[jb.path_off + tmid] = q;
-    a.sval[jb.aux_off + tmid] = ssnap[q];
-  }
+}
+
+// exact decoding: one CTA per sequence; other kinds: a persistent grid of
+// the CTAs resident at once (per instance), at most one per job
+template <int KM, bool VAN>
+static cudaError_t launch_small_cfg(const DenseArgs& a, int jobs, cudaStream_t st) {
+  const size_t sm = small_stage_logB<KM>(a) ? (size_t)a.V * KM * sizeof(float) : 0;
+  auto kern = small_fwd_kernel<KM, VAN>;
+  int per_sm = 0, dev = 0, nsm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KM, sm);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = VAN ? jobs : (jobs < per_sm * nsm ? jobs : per_sm * nsm);
+  kern<<<grid, KM, sm, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_small_forward(const DenseArgs& a, cudaStream_t st) {
   if (a.K > 128) return cudaErrorInvalidValue;
-  const int grid = (a.kind == kJobVanilla || a.kind == kJobRoot) ? a.order_count : a.max_jobs;
-  if (grid <= 0) return cudaSuccess;
+  // upper bound of the launch's jobs (task lists count on the device)
+  const int jobs = (a.kind == kJobVanilla || a.kind == kJobRoot) ? a.order_count : a.max_jobs;
+  if (jobs <= 0) return cudaSuccess;
   const bool van = a.kind == kJobVanilla;
-  if (a.K <= 64) {
-    const size_t sm = small_stage_logB<64>(a) ? (size_t)a.V * 64 * sizeof(float) : 0;
-    if (van)
-      small_fwd_kernel<64, true><<<grid, 64, sm, st>>>(a);
-    else
-      small_fwd_kernel<64, false><<<grid, 64, sm, st>>>(a);
-  } else {
-    const size_t sm = small_stage_logB<128>(a) ? (size_t)a.V * 128 * sizeof(float) : 0;
-    if (van)
-      small_fwd_kernel<128, true><<<grid, 128, sm, st>>>(a);
-    else
-      small_fwd_kernel<128, false><<<grid, 128, sm, st>>>(a);
-  }
-  return cudaGetLastError();
+  if (a.K <= 64) return van ? launch_small_cfg<64, true>(a, jobs, st) : launch_small_cfg<64, false>(a, jobs, st);
+  return van ? launch_small_cfg<128, true>(a, jobs, st) : launch_small_cfg<128, false>(a, jobs, st);
 }
 
 }  // namespace fv
