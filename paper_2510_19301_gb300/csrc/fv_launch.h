@@ -213,7 +213,8 @@ int device_sm_count();
 bool wide_geometry(int K, int nsm, WideGeom* g);
 size_t wide_scratch_bytes(int K, int nsm);
 cudaError_t launch_wide_forward(DenseArgs a, cudaStream_t st);
-// exact (vanilla) jobs with K <= 128: one CTA per sequence, a thread per state
+// small state spaces (K <= 128), every job kind: a CTA of K-class threads per
+// job, a thread per state (fv_small.cu)
 cudaError_t launch_small_forward(const DenseArgs& a, cudaStream_t st);
 // AT[j * KD + i] = logA[i * K + j] (rows K..KD-1 are -inf), KD = wide_lane_stride(K).
 cudaError_t launch_wide_transpose(const float* logA, int K, float* AT, cudaStream_t st);
