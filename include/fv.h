@@ -234,9 +234,11 @@ fv_status fv_timing_read(float* total_ms, int32_t* n_pairs);
 fv_status fv_timing_pairs(float* ms, int32_t max_pairs, int32_t* n_pairs);
 
 /* Autotuning of the exact forward engine (not in the paper).  Dense exact
- * decoding has, per class of K (<= 64, <= 128, <= 256), several engine
- * configurations -- warps per CTA and columns per lane -- that compute the
- * same values in the same order and differ only in speed.  fv_autotune
+ * decoding has, per class of K (<= 64, <= 128, <= 256, <= 512, <= 1024),
+ * several engine configurations -- the one-CTA-per-job small-K engine
+ * (K <= 128), cluster sizes, CTAs per SM, warps per CTA and columns per
+ * lane -- that compute the same values in the same order and differ only
+ * in speed.  fv_autotune
  * decodes the given request once per candidate of every class present
  * (one warm-up and two timed calls each, CUDA events on `stream`), keeps
  * the fastest per class for every later fv_decode in this process, and
