@@ -116,12 +116,12 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
     const int tmid = (m + n) / 2;  // sub jobs
     // E_{t}, ..., E_{t+kSmallAhead-1} of this state, oldest first
     float er[kSmallAhead];
-  #pragma unroll
+#pragma unroll
     for (int k = 0; k < kSmallAhead; ++k) er[k] = (own && m + k <= n) ? small_emit<KM>(a, jb, m + k, j, sB) : 0.f;
     int cur = 0;
     for (int t = m; t <= n; ++t) {
       const float e = er[0];
-  #pragma unroll
+#pragma unroll
       for (int k = 0; k + 1 < kSmallAhead; ++k) er[k] = er[k + 1];
       er[kSmallAhead - 1] = (own && t + kSmallAhead <= n) ? small_emit<KM>(a, jb, t + kSmallAhead, j, sB) : 0.f;
       float dval;
@@ -144,14 +144,14 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
         const float4* dv = reinterpret_cast<const float4*>(sd[cur]);
         float bq[4];
         int gq[4];
-  #pragma unroll
+#pragma unroll
         for (int q = 0; q < 4; ++q) {
           bq[q] = -CUDART_INF_F;
           gq[q] = q * Q;
         }
-  #pragma unroll
+#pragma unroll
         for (int i4 = 0; i4 < Q / 4; ++i4)
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int i = q * Q + 4 * i4;
             const float4 x = dv[i / 4];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
           }
         float bv = bq[0];
         g = gq[0];
-  #pragma unroll
+#pragma unroll
         for (int q = 1; q < 4; ++q)
           if (bq[q] > bv) { bv = bq[q]; g = gq[q]; }
         dval = own ? __fadd_rn(bv, e) : -CUDART_INF_F;
@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
       // termination: q_{T-1} = lowest argmax_j delta_{T-1}[j], score = delta_{T-1}[q]
       float v = sd[cur][j];
       int qi = j;
-  #pragma unroll
+#pragma unroll
       for (int k = 1; k < KM / 32; ++k) {
         const float vk = sd[cur][j + 32 * k];
         if (vk > v) { v = vk; qi = j + 32 * k; }
       }
-  #pragma unroll
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oq = __shfl_xor_sync(0xffffffffu, qi, o);
