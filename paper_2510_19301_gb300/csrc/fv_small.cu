@@ -6,9 +6,10 @@
 // the division points, FLASH subtasks from the pruned start (Alg. 2,
 // Sec. V-B.2), budget leaves and Checkpoint Viterbi passes.
 //
-// Thread j owns target state j and keeps the column logA[:, j] in
+// Target state j is owned by one thread (two for exact decoding, each with
+// half of the rows) that keeps its part of the column logA[:, j] in
 // registers; delta_{t-1} sits in shared memory (double buffered) and every
-// thread reads it as broadcast rows.  Per step the thread forms the K
+// thread reads it as broadcast rows.  Per step the thread forms its
 // candidates fl(delta_{t-1}[i] + logA[i][j]) in ascending i, in four
 // interleaved chains over quarters of the rows, keeping the first strictly
 // larger candidate and its row; the quarters merge in row order, so ties
@@ -44,30 +45,39 @@ __device__ __forceinline__ float small_emit(const DenseArgs& a, const Job& jb, i
   return sB ? sB[x * KM + j] : __ldg(a.logB + (int64_t)j * a.V + x);
 }
 constexpr int kSmallAhead = 4;  // emission scores loaded this many steps ahead
+// threads per state: exact decoding runs two (each the argmax over half of
+// the rows; the pair merges with one shuffle of adjacent lanes and the
+// first writes), the other job kinds one (measured: two threads cut a lone
+// K=64 sequence by 18% and slowed the FLASH levels of config 4 by 18%)
+template <bool VAN>
+__host__ __device__ constexpr int small_tpc() { return VAN ? 2 : 1; }
 
 // VAN: the exact-decoding instance (no MidState, snapshots or task lists,
 // fewer registers); otherwise every job kind of the engines
 template <int KM, bool VAN>
-__global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
-  constexpr int Q = KM / 4;  // rows per chain
+__global__ void __launch_bounds__(KM * small_tpc<VAN>(), VAN ? (KM <= 64 ? 6 : 2) : (KM <= 64 ? 8 : 1)) small_fwd_kernel(DenseArgs a) {
+  constexpr int TPC = small_tpc<VAN>(), RH = KM / TPC;  // threads per state, rows per thread
+  constexpr int Q = RH / 4;                      // rows per chain
   __shared__ __align__(16) float sd[2][KM];
   __shared__ uint16_t smid[2][KM];  // MidState_{t-1}, MidState_t
   __shared__ float ssnap[KM];       // sub jobs: delta_{tmid}
   extern __shared__ float sB_dyn[];
   if (a.hdr->status != 0) return;  // an earlier kernel recorded an error
-  const int kind = VAN ? (int)kJobVanilla : a.kind, K = a.K, j = threadIdx.x;
-  const bool own = j < K;
+  const int kind = VAN ? (int)kJobVanilla : a.kind, K = a.K, tid = threadIdx.x;
+  const int j = tid / TPC, h = tid % TPC, r0 = h * RH;  // state, row share, its first row
+  const bool own = j < K, lead = h == 0;
   // rows and states beyond K are -inf, so they never win; the model is the
   // same for every job of the launch, so the column stays in registers
-  float A[KM];
+  float A[RH];
   auto load_column = [&]() {
 #pragma unroll
-    for (int i = 0; i < KM; ++i) A[i] = (own && i < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
+    for (int i = 0; i < RH; ++i)
+      A[i] = (own && r0 + i < K) ? __ldg(a.logA + (int64_t)(r0 + i) * K + j) : -CUDART_INF_F;
   };
   if constexpr (!VAN) load_column();
   const float* sB = nullptr;
   if (small_stage_logB<KM>(a)) {
-    for (int x = 0; x < a.V; ++x) sB_dyn[x * KM + j] = own ? __ldg(a.logB + (int64_t)j * a.V + x) : 0.f;
+    for (int x = h; x < a.V; x += TPC) sB_dyn[x * KM + j] = own ? __ldg(a.logB + (int64_t)j * a.V + x) : 0.f;
     sB = sB_dyn;
   }
   // exact decoding: one job per CTA (grid = sequences); other kinds:
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
         s_prev = a.sval[jb.aux_off + m - 1];
       }
     }
-    if (!VAN) {
+    if (!VAN && lead) {
       smid[0][j] = smid[1][j] = 0;
       ssnap[j] = -CUDART_INF_F;
     }
@@ -147,30 +157,38 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           bq[q] = -CUDART_INF_F;
-          gq[q] = q * Q;
+          gq[q] = r0 + q * Q;
         }
 #pragma unroll
         for (int i4 = 0; i4 < Q / 4; ++i4)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int i = q * Q + 4 * i4;
-            const float4 x = dv[i / 4];
+            const int i = q * Q + 4 * i4;  // local row; global r0 + i
+            const float4 x = dv[(r0 + i) / 4];
             float c = __fadd_rn(x.x, A[i]);
-            if (c > bq[q]) { bq[q] = c; gq[q] = i; }
+            if (c > bq[q]) { bq[q] = c; gq[q] = r0 + i; }
             c = __fadd_rn(x.y, A[i + 1]);
-            if (c > bq[q]) { bq[q] = c; gq[q] = i + 1; }
+            if (c > bq[q]) { bq[q] = c; gq[q] = r0 + i + 1; }
             c = __fadd_rn(x.z, A[i + 2]);
-            if (c > bq[q]) { bq[q] = c; gq[q] = i + 2; }
+            if (c > bq[q]) { bq[q] = c; gq[q] = r0 + i + 2; }
             c = __fadd_rn(x.w, A[i + 3]);
-            if (c > bq[q]) { bq[q] = c; gq[q] = i + 3; }
+            if (c > bq[q]) { bq[q] = c; gq[q] = r0 + i + 3; }
           }
         float bv = bq[0];
         g = gq[0];
 #pragma unroll
         for (int q = 1; q < 4; ++q)
           if (bq[q] > bv) { bv = bq[q]; g = gq[q]; }
+        if constexpr (TPC == 2) {
+          // the pair's merge: the lower rows (h = 0) win ties; both threads
+          // end with the same (maximum, row)
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, 1);
+          const int og = __shfl_xor_sync(0xffffffffu, g, 1);
+          const bool other = h == 0 ? (ov > bv) : !(bv > ov);
+          if (other) { bv = ov; g = og; }
+        }
         dval = own ? __fadd_rn(bv, e) : -CUDART_INF_F;
-        if (own && (kind == kJobVanilla || kind == kJobLeaf)) {
+        if (lead && own && (kind == kJobVanilla || kind == kJobLeaf)) {
           const int64_t row = kind == kJobVanilla ? jb.aux_off + (int64_t)t * K
                               : a.ckpt        ? 2 * (jb.aux_off + (int64_t)Pe * K) + (int64_t)(t - m - 1) * K
                                               : (int64_t)(pad + t - m - 1) * K;
@@ -182,13 +200,13 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
         if (kind == kJobSub) f_mid = (t == tmid + 1) ? 1 : (t > tmid + 1 ? 2 : 0);
         if (f_mid) mnew = f_mid == 1 ? (uint32_t)g : smid[cur][g];
         // sub jobs keep delta_{tmid} (the previous step's delta)
-        if (kind == kJobSub && t == tmid + 1) ssnap[j] = sd[cur][j];
+        if (lead && kind == kJobSub && t == tmid + 1) ssnap[j] = sd[cur][j];
       }
-      if (f_mid) smid[cur ^ 1][j] = (uint16_t)mnew;
+      if (lead && f_mid) smid[cur ^ 1][j] = (uint16_t)mnew;
       if (kind == kJobRoot && t == ediv) {
         // division point: delta snapshot and, from the second one on, the
         // ancestor map (MidState); checkpoints keep delta only
-        if (own) {
+        if (lead && own) {
           if (a.ckpt) {
             a.snaps[jb.aux_off + (int64_t)kdiv * K + j] = dval;
           } else {
@@ -200,18 +218,18 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
         ++kdiv;
         ediv = kdiv < Pe ? flash_div(kdiv, T, Pe) : 0x7fffffff;
       }
-      sd[cur ^ 1][j] = dval;
+      if (lead) sd[cur ^ 1][j] = dval;
       __syncthreads();
       cur ^= 1;
     }
-    if (kind == kJobVanilla && j < 32) {
+    if (kind == kJobVanilla && tid < 32) {
       // termination: q_{T-1} = lowest argmax_j delta_{T-1}[j], score = delta_{T-1}[q]
-      float v = sd[cur][j];
-      int qi = j;
+      float v = sd[cur][tid];
+      int qi = tid;
 #pragma unroll
       for (int k = 1; k < KM / 32; ++k) {
-        const float vk = sd[cur][j + 32 * k];
-        if (vk > v) { v = vk; qi = j + 32 * k; }
+        const float vk = sd[cur][tid + 32 * k];
+        if (vk > v) { v = vk; qi = tid + 32 * k; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -219,11 +237,11 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
         const int oq = __shfl_xor_sync(0xffffffffu, qi, o);
         if (ov > v || (ov == v && oq < qi)) { v = ov; qi = oq; }
       }
-      if (j == 0) {
+      if (tid == 0) {
         a.qlast[b] = qi;
         a.scores[b] = sd[cur][qi];
       }
-    } else if (kind == kJobSub && j == 0) {
+    } else if (kind == kJobSub && tid == 0) {
       // Alg. 2 output: q*_{tmid} = MidState_n[q*_n]; its delta from the snapshot
       int q = smid[cur][q_n];
       q = (unsigned)q < (unsigned)K ? q : 0;
@@ -236,7 +254,7 @@ __global__ void __launch_bounds__(KM) small_fwd_kernel(DenseArgs a) {
     if ((int)blockIdx.x < count) run_job(blockIdx.x);
   } else {
     for (;;) {
-      if (j == 0) s_k = (int)atomicAdd(a.pop, 1ull);
+      if (tid == 0) s_k = (int)atomicAdd(a.pop, 1ull);
       __syncthreads();
       const int k = s_k;
       __syncthreads();
@@ -253,13 +271,13 @@ static cudaError_t launch_small_cfg(const DenseArgs& a, int jobs, cudaStream_t s
   const size_t sm = small_stage_logB<KM>(a) ? (size_t)a.V * KM * sizeof(float) : 0;
   auto kern = small_fwd_kernel<KM, VAN>;
   int per_sm = 0, dev = 0, nsm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KM, sm);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KM * small_tpc<VAN>(), sm);
   if (e != cudaSuccess) return e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = VAN ? jobs : (jobs < per_sm * nsm ? jobs : per_sm * nsm);
-  kern<<<grid, KM, sm, st>>>(a);
+  kern<<<grid, KM * small_tpc<VAN>(), sm, st>>>(a);
   return cudaGetLastError();
 }
 
