@@ -45,18 +45,18 @@ __device__ __forceinline__ float small_emit(const DenseArgs& a, const Job& jb, i
   return sB ? sB[x * KM + j] : __ldg(a.logB + (int64_t)j * a.V + x);
 }
 constexpr int kSmallAhead = 4;  // emission scores loaded this many steps ahead
-// threads per state: exact decoding runs two (each the argmax over half of
-// the rows; the pair merges with one shuffle of adjacent lanes and the
-// first writes), the other job kinds one (measured: two threads cut a lone
-// K=64 sequence by 18% and slowed the FLASH levels of config 4 by 18%)
-template <bool VAN>
-__host__ __device__ constexpr int small_tpc() { return VAN ? 2 : 1; }
-
+// TPC = threads per state: with two, each runs the argmax over half of the
+// rows, the pair merges with one shuffle of adjacent lanes and the first
+// writes.  Exact decoding always runs two; the other job kinds run two
+// when the launch's jobs all fit the resident grid at once (a lone
+// sequence's FLASH levels), else one (twice the jobs in flight: measured,
+// two threads cut config 1's FLASH decode by 12% and slowed a 512-sequence
+// K=64 FLASH batch by 45%).
 // VAN: the exact-decoding instance (no MidState, snapshots or task lists,
 // fewer registers); otherwise every job kind of the engines
-template <int KM, bool VAN>
-__global__ void __launch_bounds__(KM * small_tpc<VAN>(), VAN ? (KM <= 64 ? 6 : 2) : (KM <= 64 ? 8 : 1)) small_fwd_kernel(DenseArgs a) {
-  constexpr int TPC = small_tpc<VAN>(), RH = KM / TPC;  // threads per state, rows per thread
+template <int KM, bool VAN, int TPC>
+__global__ void __launch_bounds__(KM * TPC, VAN ? (KM <= 64 ? 6 : 2) : (KM <= 64 ? 8 / TPC : 1)) small_fwd_kernel(DenseArgs a) {
+  constexpr int RH = KM / TPC;  // rows per thread
   constexpr int Q = RH / 4;                      // rows per chain
   __shared__ __align__(16) float sd[2][KM];
   __shared__ uint16_t smid[2][KM];  // MidState_{t-1}, MidState_t
@@ -266,19 +266,35 @@ __global__ void __launch_bounds__(KM * small_tpc<VAN>(), VAN ? (KM <= 64 ? 6 : 2
 
 // exact decoding: one CTA per sequence; other kinds: a persistent grid of
 // the CTAs resident at once (per instance), at most one per job
-template <int KM, bool VAN>
-static cudaError_t launch_small_cfg(const DenseArgs& a, int jobs, cudaStream_t st) {
-  const size_t sm = small_stage_logB<KM>(a) ? (size_t)a.V * KM * sizeof(float) : 0;
-  auto kern = small_fwd_kernel<KM, VAN>;
+// CTAs of the instance resident at once on the device (0 on an error)
+template <int KM, bool VAN, int TPC>
+static int small_resident(size_t sm) {
   int per_sm = 0, dev = 0, nsm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KM * small_tpc<VAN>(), sm);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int grid = VAN ? jobs : (jobs < per_sm * nsm ? jobs : per_sm * nsm);
-  kern<<<grid, KM * small_tpc<VAN>(), sm, st>>>(a);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, small_fwd_kernel<KM, VAN, TPC>, KM * TPC, sm) !=
+          cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * nsm;
+}
+
+template <int KM, bool VAN, int TPC>
+static cudaError_t launch_small_cfg(const DenseArgs& a, int jobs, int resident, cudaStream_t st) {
+  const size_t sm = small_stage_logB<KM>(a) ? (size_t)a.V * KM * sizeof(float) : 0;
+  if (resident < 1) return cudaErrorInvalidConfiguration;
+  const int grid = VAN ? jobs : (jobs < resident ? jobs : resident);
+  small_fwd_kernel<KM, VAN, TPC><<<grid, KM * TPC, sm, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int KM>
+static cudaError_t launch_small_class(const DenseArgs& a, int jobs, cudaStream_t st) {
+  const size_t sm = small_stage_logB<KM>(a) ? (size_t)a.V * KM * sizeof(float) : 0;
+  if (a.kind == kJobVanilla) return launch_small_cfg<KM, true, 2>(a, jobs, small_resident<KM, true, 2>(sm), st);
+  const int r2 = small_resident<KM, false, 2>(sm);
+  if (jobs <= r2) return launch_small_cfg<KM, false, 2>(a, jobs, r2, st);
+  return launch_small_cfg<KM, false, 1>(a, jobs, small_resident<KM, false, 1>(sm), st);
 }
 
 cudaError_t launch_small_forward(const DenseArgs& a, cudaStream_t st) {
@@ -286,9 +302,7 @@ cudaError_t launch_small_forward(const DenseArgs& a, cudaStream_t st) {
   // upper bound of the launch's jobs (task lists count on the device)
   const int jobs = (a.kind == kJobVanilla || a.kind == kJobRoot) ? a.order_count : a.max_jobs;
   if (jobs <= 0) return cudaSuccess;
-  const bool van = a.kind == kJobVanilla;
-  if (a.K <= 64) return van ? launch_small_cfg<64, true>(a, jobs, st) : launch_small_cfg<64, false>(a, jobs, st);
-  return van ? launch_small_cfg<128, true>(a, jobs, st) : launch_small_cfg<128, false>(a, jobs, st);
+  return a.K <= 64 ? launch_small_class<64>(a, jobs, st) : launch_small_class<128>(a, jobs, st);
 }
 
 }  // namespace fv
