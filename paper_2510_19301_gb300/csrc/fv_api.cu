@@ -472,6 +472,13 @@ fv_status decode_beam(const fv_model* models, int32_t n_models, const fv_batch* 
     ba.scores = scores_out;
     ba.paths = paths_out;
     ba.hdr = hdr;
+    if (batch->T_host) {
+      for (int i = 0; i < batch->n_seq; ++i) {
+        if ((batch->model_host ? batch->model_host[i] : 0) != m) continue;
+        ba.sum_T += batch->T_host[i];
+        if (batch->T_host[i] > ba.max_T) ba.max_T = batch->T_host[i];
+      }
+    }
     if (m > 0 && launch_reset(ba.pop, st) != cudaSuccess) return FV_ECUDA;
     if (!tasks) {
       ba.kind = kJobBeam;

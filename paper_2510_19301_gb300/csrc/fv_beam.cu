@@ -4,7 +4,8 @@
 // a time (a whole sequence, or one Alg. 1 segment task) and pops the next
 // job from a global counter.  Beams of at least 64 states on large CSR state
 // spaces (P = 0) instead spread each sequence over a cluster of CTAs
-// (beam_csr_cluster_kernel, below).  A beam
+// (beam_csr_cluster_kernel, below), and so do dense beams with
+// 512 <= K <= 8192 (P = 0; beam_dense_cluster_kernel).  A beam
 // is the top-B finite candidates under (score desc, state id asc); it is
 // kept sorted by state id so that the next step visits its sources in
 // ascending order.  Per step:
@@ -26,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "fv_internal.cuh"
 #include "fv_launch.h"
@@ -893,7 +896,17 @@ __global__ void __launch_bounds__(kCBThreads, 1) beam_csr_cluster_kernel(BeamArg
     base += align_up((size_t)a.Bcap * 4);
     base += 2 * align_up((size_t)a.Bcap * 4);  // (mid, src: unused here)
   }
-  if (a.hdr->status != 0) return;  // read by every CTA before any work: a cluster-uniform decision
+  // every CTA of the cluster has started before shared memory is written
+  // remotely; one thread of rank 0 reads the status word and tells the
+  // others, so the decision to run is the same in every CTA
+  __shared__ int s_go;
+  cluster_sync_all();
+  if (rank == 0 && tid == 0) {
+    const uint32_t go = a.hdr->status == 0 ? 1u : 0u;
+    for (int q = 0; q < kCB; ++q) dsmem_st_u32(dsmem_addr(&s_go, (uint32_t)q), go);
+  }
+  cluster_sync_all();
+  if (!s_go) return;
   for (int w = tid; w < bm_words; w += blockDim.x) bitmap[w] = 0u;
   for (int j = j_lo + tid; j < j_hi; j += blockDim.x) keys[j] = 0ull;
   cluster_sync_all();
@@ -1121,6 +1134,341 @@ __global__ void __launch_bounds__(kCBThreads, 1) beam_csr_cluster_kernel(BeamArg
   }
 }
 
+// ---------------------------------------------------------------------------
+// Dynamic beam on dense transitions with one sequence spread over a cluster
+// of kDC CTAs (kJobBeam, 512 <= K <= 8192).  A dense step reads B rows of
+// logA (B K cells); on one SM its time is set by how fast those rows come in
+// from L2.  Here CTA r owns the targets [r R, (r+1) R), R = K / kDC:
+//  * candidates: its threads split (target quad, beam slot residue); every
+//    thread reads 16-byte pieces of the beam sources' logA rows (a warp
+//    reads whole row pieces), keeps per target the highest value, lowest
+//    slot on ties, and the partials are combined through shared memory;
+//    c_j = fl(M_j + E_t[j]) is then stored into the candidate vector of
+//    every CTA of the cluster (distributed shared memory, double-buffered by
+//    step parity);
+//  * one cluster barrier: every CTA now holds all K candidates;
+//  * top-B select: each CTA runs the same MSB radix select (order-preserving
+//    keys, -0 folded into +0) over the K candidates and builds the next beam
+//    in id order in its own shared memory, so the next step reads its
+//    sources locally; each CTA writes the backpointers of its own targets.
+// Same candidates, same tie rules and the same beams as the single-CTA
+// kernel, hence the same paths and scores.
+constexpr int kDC = 8;  // CTAs per sequence
+constexpr int kDCThreads = 512;
+constexpr int kDCMaxK = 8192;
+constexpr int kDCKeys = kDCMaxK / kDCThreads;  // candidate keys per thread
+
+struct DcLayout {
+  int R, Q, S, G2, RS;  // targets per CTA, their quads, slot groups, lanes per target, partial row stride
+  size_t words;         // dynamic shared memory (4-byte words)
+};
+
+__host__ __device__ inline DcLayout dc_layout(int K, int W) {
+  DcLayout L;
+  L.R = K / kDC;
+  L.Q = L.R / 4;
+  L.S = kDCThreads / L.Q;
+  L.G2 = 1;
+  while (2 * L.G2 * L.R <= kDCThreads) L.G2 *= 2;
+  // padding that puts the G2 lanes of a target on distinct banks
+  const int pad = 32 / L.G2 > 4 ? 32 / L.G2 : 4;
+  L.RS = L.R + pad;
+  // [2][K] candidates, [S][RS] partial values and slots, [3][256] histograms,
+  // [R] slots of this CTA's targets, [W] beam ids, [W] beam scores
+  L.words = 2 * (size_t)K + 2 * (size_t)L.S * L.RS + 768 + (size_t)L.R + 2 * (size_t)W;
+  return L;
+}
+
+// Exclusive scan of two per-thread counts over the block (kDCThreads).
+__device__ inline void dc_scan2(int x, int y, int* red, int* ex, int* ey, int* tx, int* ty) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int sx = x, sy = y;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ux = __shfl_up_sync(0xffffffffu, sx, o), uy = __shfl_up_sync(0xffffffffu, sy, o);
+    if (lane >= o) { sx += ux; sy += uy; }
+  }
+  if (lane == 31) { red[w] = sx; red[16 + w] = sy; }
+  __syncthreads();
+  if (w == 0) {
+    int px = lane < 16 ? red[lane] : 0, py = lane < 16 ? red[16 + lane] : 0;
+    for (int o = 1; o < 16; o <<= 1) {
+      const int ux = __shfl_up_sync(0xffffffffu, px, o), uy = __shfl_up_sync(0xffffffffu, py, o);
+      if (lane >= o) { px += ux; py += uy; }
+    }
+    if (lane < 16) { red[lane] = px; red[16 + lane] = py; }
+  }
+  __syncthreads();
+  *ex = (w ? red[w - 1] : 0) + sx - x;
+  *ey = (w ? red[16 + w - 1] : 0) + sy - y;
+  *tx = red[15];
+  *ty = red[31];
+  // (red is written again only after the caller's next block barrier)
+}
+
+__global__ void __launch_bounds__(kDCThreads, 1) beam_dense_cluster_kernel(BeamArgs a) {
+  extern __shared__ __align__(16) uint32_t dsm[];
+  __shared__ int red[32];
+  __shared__ int s_go, s_job;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int K = a.K, W = a.Wcap < a.Bcap ? a.Wcap : a.Bcap;
+  const DcLayout L = dc_layout(K, W);
+  const int R = L.R, j_lo = (int)rank * R;
+  float* cand = reinterpret_cast<float*>(dsm);                      // [2][K]
+  float* pv = cand + 2 * K;                                          // [S][RS]
+  int32_t* ps = reinterpret_cast<int32_t*>(pv + L.S * L.RS);        // [S][RS]
+  int* hist = reinterpret_cast<int*>(ps + L.S * L.RS);               // [3][256]
+  int32_t* lslot = hist + 768;                                       // [R]
+  int32_t* bid = lslot + R;                                          // [W]
+  float* bval = reinterpret_cast<float*>(bid + W);                   // [W]
+  for (int k = tid; k < 768; k += blockDim.x) hist[k] = 0;
+  // every CTA of the cluster has started before shared memory is written
+  // remotely; one thread of rank 0 reads the status word and tells the
+  // others, so the decision to run is the same in every CTA
+  cluster_sync_all();
+  if (rank == 0 && tid == 0) {
+    const uint32_t go = a.hdr->status == 0 ? 1u : 0u;
+    for (int q = 0; q < kDC; ++q) dsmem_st_u32(dsmem_addr(&s_go, (uint32_t)q), go);
+  }
+  cluster_sync_all();
+  if (!s_go) return;
+
+  // candidates: thread (quad qd, slot group sg)
+  const int qd = tid % L.Q, sg = tid / L.Q;
+  const bool cact = sg < L.S;
+  const int K4 = K >> 2;
+  const float4* arow = reinterpret_cast<const float4*>(a.logA) + (j_lo >> 2) + qd;
+  // final combine: G2 lanes per target, NG targets per round (at most 2 rounds)
+  const int G2 = L.G2, NG = kDCThreads / G2, sub = tid % G2;
+  // select: keys strided over the block, compaction over contiguous id ranges
+  const int per = (K + kDCThreads - 1) / kDCThreads;  // also the keys per thread
+  const int c0 = min(K, tid * per), c1 = min(K, c0 + per);
+  int hrot = 0;  // histogram buffer of the next radix pass
+
+  for (;;) {
+    // the next sequence (longest first) for the whole cluster: rank 0 takes
+    // it from the launch's counter and tells the others
+    if (rank == 0 && tid == 0) {
+      const unsigned long long k = atomicAdd(a.pop, 1ull);
+      const uint32_t jk = k < (unsigned long long)a.order_count ? (uint32_t)k : 0xFFFFFFFFu;
+      for (int q = 0; q < kDC; ++q) dsmem_st_u32(dsmem_addr(&s_job, (uint32_t)q), jk);
+    }
+    cluster_sync_all();
+    const int jk = s_job;
+    if (jk < 0) break;  // every CTA of the cluster leaves together
+    const int b = a.order[a.order_begin + jk];
+    const Job jb = a.jobs[b];
+    const int T = jb.T;
+    int nb = 0;
+    bool infeasible = false;
+    for (int t = 0; t < T && !infeasible; ++t) {
+      const int buf = t & 1;
+      float* cv = cand + buf * K;
+      // this step's emission scores of the thread's final targets
+      float ev[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int x = r * NG + tid / G2;
+        ev[r] = x < R ? beam_emit(a, jb, t, j_lo + x) : 0.f;
+      }
+      if (a.emit == FV_EMIT_DENSE && tid == 0 && t + 1 < T) {
+        const float* row = a.E + jb.e_off + (int64_t)(t + 1) * K + j_lo;
+        if (((uintptr_t)row & 15u) == 0) prefetch_l2_bulk(row, (uint32_t)R * 4u);
+      }
+      if (t == 0) {
+        for (int r = 0; r < 2; ++r) {
+          const int x = r * NG + tid / G2;
+          if (x < R && sub == 0) {
+            const float c = __fadd_rn(__ldg(a.log_pi + j_lo + x), ev[r]);
+            for (int q = 0; q < kDC; ++q) dsmem_st_f32(dsmem_addr(&cv[j_lo + x], (uint32_t)q), c);
+          }
+        }
+      } else {
+        // ---- candidates of this CTA's targets from the local beam
+        float best[4];
+        int sl[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          best[c] = -CUDART_INF_F;
+          sl[c] = -1;
+        }
+        if (cact) {
+          auto take = [&](int k, float4 w) {
+            const float v = bval[k];
+            const float x0 = __fadd_rn(v, w.x), x1 = __fadd_rn(v, w.y), x2 = __fadd_rn(v, w.z),
+                        x3 = __fadd_rn(v, w.w);
+            if (sl[0] < 0 || x0 > best[0]) { best[0] = x0; sl[0] = k; }
+            if (sl[1] < 0 || x1 > best[1]) { best[1] = x1; sl[1] = k; }
+            if (sl[2] < 0 || x2 > best[2]) { best[2] = x2; sl[2] = k; }
+            if (sl[3] < 0 || x3 > best[3]) { best[3] = x3; sl[3] = k; }
+          };
+          const int S = L.S;
+          int k = sg;
+          // eight sources in flight per round; compared in slot order
+          for (; k + 7 * S < nb; k += 8 * S) {
+            float4 w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) w[u] = __ldg(arow + (int64_t)bid[k + u * S] * K4);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) take(k + u * S, w[u]);
+          }
+          for (; k < nb; k += S) take(k, __ldg(arow + (int64_t)bid[k] * K4));
+          reinterpret_cast<float4*>(pv + sg * L.RS)[qd] = make_float4(best[0], best[1], best[2], best[3]);
+          reinterpret_cast<int4*>(ps + sg * L.RS)[qd] = make_int4(sl[0], sl[1], sl[2], sl[3]);
+        }
+        __syncthreads();
+        // ---- combine the slot groups per target, add E, send to every CTA
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (r * NG >= R) break;  // uniform
+          const int x = r * NG + tid / G2;
+          float bv = -CUDART_INF_F;
+          int bs = -1;
+          if (x < R)
+            for (int s = sub; s < L.S; s += G2) {
+              const float v = pv[s * L.RS + x];
+              const int q = ps[s * L.RS + x];
+              if (q >= 0 && (bs < 0 || v > bv || (v == bv && q < bs))) { bv = v; bs = q; }
+            }
+          for (int o = 1; o < G2; o <<= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+            if (os >= 0 && (bs < 0 || ov > bv || (ov == bv && os < bs))) { bv = ov; bs = os; }
+          }
+          if (x < R) {
+            const float c = __fadd_rn(bv, ev[r]);
+            for (int q = sub; q < kDC; q += G2) dsmem_st_f32(dsmem_addr(&cv[j_lo + x], (uint32_t)q), c);
+            if (sub == 0) lslot[x] = bs;
+          }
+        }
+      }
+      cluster_sync_all();  // every CTA holds the K candidates of step t
+      // ---- top-W of the K candidates (finite only): score desc, id asc
+      uint32_t ku[kDCKeys];
+#pragma unroll
+      for (int i = 0; i < kDCKeys; ++i) {
+        if (i >= per) break;  // uniform
+        const int j = tid + i * kDCThreads;
+        const float c = j < K ? cv[j] : -CUDART_INF_F;
+        ku[i] = isfinite(c) ? ord_key(c) : 0u;
+      }
+      uint32_t prefix = 0u, mask = 0u, thr_gt = 0u;
+      int remaining = W, need_eq = 0;
+      for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        // three histogram buffers in rotation: the one counted two passes
+        // ago is cleared while this one is read, so every pass needs one
+        // block barrier
+        const int hb = hrot;
+        hrot = hrot == 2 ? 0 : hrot + 1;
+        int* h = hist + hb * 256;
+#pragma unroll
+        for (int i = 0; i < kDCKeys; ++i) {
+          if (i >= per) break;  // uniform
+          const uint32_t u = ku[i];
+          const bool ok = u != 0u && (u & mask) == prefix;
+          const int d = ok ? (int)((u >> shift) & 0xFFu) : -1;
+          const unsigned grp = __match_any_sync(0xffffffffu, d);
+          if (ok && lane == __ffs(grp) - 1) atomicAdd(&h[d], __popc(grp));
+        }
+        __syncthreads();
+        if (tid < 256) hist[(hb == 0 ? 2 : hb - 1) * 256 + tid] = 0;
+        // every warp finds the digit from the same histogram: lane l holds
+        // digits 255-8l .. 248-8l
+        int hv[8], sum = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          hv[u] = h[255 - 8 * lane - u];
+          sum += hv[u];
+        }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (pass == 0 && total <= remaining) {
+          thr_gt = 0u;  // every finite candidate fits
+          need_eq = 0;
+          break;
+        }
+        const int excl = incl - sum;
+        const unsigned hit = __ballot_sync(0xffffffffu, excl < remaining && remaining <= incl);
+        int acc = excl, u_hit = 7;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (acc + hv[u] >= remaining) { u_hit = u; break; }
+          acc += hv[u];
+        }
+        const int src = __ffs(hit) - 1;
+        const int dg = __shfl_sync(0xffffffffu, 255 - 8 * lane - u_hit, src);
+        const int rem = __shfl_sync(0xffffffffu, remaining - acc, src);
+        const int whole = __shfl_sync(0xffffffffu, hv[u_hit], src) == rem;
+        prefix |= (uint32_t)dg << shift;
+        mask |= 0xFFu << shift;
+        remaining = rem;
+        if (whole) {
+          // the whole bin is needed: keys >= prefix; finite keys are
+          // positive, so prefix 0 takes them all
+          thr_gt = prefix ? prefix - 1u : 0u;
+          need_eq = 0;
+          break;
+        }
+        if (pass == 3) {
+          thr_gt = prefix;
+          need_eq = remaining;
+        }
+      }
+      const uint32_t thr_eq = prefix;
+      int n_gt = 0, n_eq = 0;
+      for (int j = c0; j < c1; ++j) {
+        const float c = cv[j];
+        const uint32_t u = isfinite(c) ? ord_key(c) : 0u;
+        if (u == 0u) continue;
+        if (u > thr_gt) ++n_gt;
+        else if (need_eq > 0 && u == thr_eq) ++n_eq;
+      }
+      int gt_before, eq_before, tot_gt, tot_eq;
+      dc_scan2(n_gt, n_eq, red, &gt_before, &eq_before, &tot_gt, &tot_eq);
+      const int take_eq = min(max(need_eq - eq_before, 0), n_eq);
+      int o = gt_before + min(eq_before, need_eq);
+      nb = tot_gt + min(tot_eq, need_eq);
+      int eq_seen = 0;
+      for (int j = c0; j < c1; ++j) {
+        const float c = cv[j];
+        const uint32_t u = isfinite(c) ? ord_key(c) : 0u;
+        if (u == 0u) continue;
+        bool tk = u > thr_gt;
+        if (!tk && need_eq > 0 && u == thr_eq) tk = eq_seen++ < take_eq;
+        if (!tk) continue;
+        bid[o] = j;
+        bval[o] = c;
+        if (j >= j_lo && j < j_lo + R) {
+          a.bp_id[jb.aux_off + (int64_t)t * a.Wcap + o] = j;
+          a.bp_src[jb.aux_off + (int64_t)t * a.Wcap + o] = t == 0 ? 0 : lslot[j - j_lo];
+        }
+        ++o;
+      }
+      __syncthreads();  // the next beam is complete in this CTA
+      if (nb == 0) infeasible = true;
+    }
+    if (!infeasible) {
+      if (rank == 0 && tid == 0) {
+        int kb = 0;  // best final entry: highest score, lowest id
+        for (int e = 1; e < nb; ++e)
+          if (bval[e] > bval[kb]) kb = e;
+        a.scores[b] = bval[kb];
+        a.qlast[b] = kb;
+      }
+    } else if (rank == 0 && tid == 0) {
+      set_status(a.hdr, FV_EINFEASIBLE, (uint32_t)b);
+    }
+    // no CTA takes the next sequence (and overwrites s_job) while another
+    // still reads this one's candidates or job index
+    cluster_sync_all();
+  }
+}
+
 // Backtrack through per-step beam backpointers (one thread per sequence).
 __global__ void beam_backtrack_kernel(const Job* jobs, const int32_t* order, int32_t begin, int32_t count,
                                       int32_t Wcap, const int32_t* bp_id, const int32_t* bp_src,
@@ -1209,6 +1557,62 @@ static int launch_beam_cluster(const BeamArgs& a, int max_jobs, cudaStream_t st,
   return 0;
 }
 
+// Dense beams with 512 <= K <= 8192 (P = 0): one cluster of kDC CTAs per
+// sequence when that finishes the launch sooner; 0 when launched, 1 when
+// not applicable.  A cluster runs a step about r times faster than one CTA
+// (measured on GB300 with 64 sequences in flight: r = 2.3 at K=1024,
+// B=256; 1.4-1.6 at B=16-64) but holds kDC SMs, so the launch takes the
+// cluster kernel when max(T_max, sum T / clusters) < r max(T_max, sum T / SMs),
+// the two makespans in units of the cluster's step time (sequences are
+// taken longest first).  Without the lengths: when every sequence gets its
+// own cluster.
+static int launch_beam_dense_cluster(const BeamArgs& a, int max_jobs, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (a.trans != FV_TRANS_DENSE || a.kind != kJobBeam || a.static_beam) return 1;
+  if (a.K < 512 || a.K > kDCMaxK || (a.K % 32) != 0 || ((uintptr_t)a.logA & 15u) != 0) return 1;
+  const int W = a.Wcap < a.Bcap ? a.Wcap : a.Bcap;
+  if (W < 1) return 1;
+  const size_t smem = 4 * dc_layout(a.K, W).words;
+  if (smem > (size_t)200 * 1024) return 1;
+  int clusters = a.max_ctas / kDC;
+  if (max_jobs < clusters) clusters = max_jobs;
+  if (clusters < 1) return 1;
+  if (cudaFuncSetAttribute(beam_dense_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kDC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kDCThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(kDC * clusters);
+  int resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, beam_dense_cluster_kernel, &cfg) != cudaSuccess || resident < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (a.max_T > 0 && a.sum_T > 0) {
+    const double r = W >= 128 ? 2.2 : 1.4;
+    const double tmax = (double)a.max_T, tsum = (double)a.sum_T;
+    const double one = std::max(tmax, tsum / (double)std::max(1, a.max_ctas));
+    const double clu = std::max(tmax, tsum / (double)resident);
+    if (!(clu < r * one)) return 1;
+  } else if (max_jobs > resident) {
+    return 1;
+  }
+  if (clusters > resident) cfg.gridDim = dim3(kDC * resident);
+  *err = cudaLaunchKernelEx(&cfg, beam_dense_cluster_kernel, a);
+  return 0;
+}
+
 cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -1216,6 +1620,7 @@ cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   {
     cudaError_t ce;
     if (launch_beam_cluster(a, max_jobs, st, &ce) == 0) return ce;
+    if (launch_beam_dense_cluster(a, max_jobs, st, &ce) == 0) return ce;
   }
   BeamArgs b = a;
   size_t smem = sizeof(uint32_t) * beam_bitmap_words(a.K);

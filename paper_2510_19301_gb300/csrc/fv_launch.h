@@ -187,6 +187,10 @@ struct BeamArgs {
   // step writes the full K-entry score vector (-inf where no beam state
   // leads) to the workspace and selects the top B from all K entries
   int32_t static_beam;
+  // lengths of the launch's sequences, from the host copy (0: not given);
+  // used only to choose between one CTA and one cluster per sequence
+  int64_t sum_T;
+  int32_t max_T;
   WsHeader* hdr;
 };
 

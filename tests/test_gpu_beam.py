@@ -134,3 +134,107 @@ def test_csr_beam_large_k_cluster_engine(fv, K, deg, B):
     E_i = [np.round(e).astype(np.float32) for e in E_list]
     m2, hmm2 = make_model(fv, lp_i, csr=(rp, col, val_i))
     run_beam(fv, m2, hmm2, E_i, B, 0)
+
+
+def _masked_model(K, rng, frac):
+    """Dense model with a fraction of the transitions absent (-inf); every
+    state keeps its self-transition."""
+    log_pi, logA = W.random_model(K, rng)
+    drop = rng.random((K, K)) < frac
+    np.fill_diagonal(drop, False)
+    logA = np.where(drop, -np.inf, logA).astype(np.float32)
+    return log_pi, logA
+
+
+@pytest.mark.parametrize("K,B", [(512, 1), (512, 64), (544, 200), (768, 7), (1024, 256), (1024, 1024),
+                                 (2048, 100), (4096, 300), (8192, 64)])
+def test_dense_beam_cluster_engine(fv, K, B):
+    """Dense beams with 512 <= K <= 8192 (P = 0) run one sequence per
+    cluster of CTAs (targets split over the CTAs, every CTA selecting the
+    top B of all K candidates): same paths and scores as the oracle, with
+    absent transitions, with integer data (equal candidates and signed
+    zeros, resolved by the lowest id), and with more sequences than the
+    GPU holds clusters."""
+    rng = np.random.default_rng(K * 3 + B)
+    log_pi, logA = _masked_model(K, rng, 0.3)
+    m, hmm = make_model(fv, log_pi, logA)
+    lengths = [1, 2, 3, 40, 120] if K <= 2048 else [1, 2, 17, 30]
+    E_list = [W.gaussian_emissions(int(t), K, rng) for t in lengths]
+    run_beam(fv, m, hmm, E_list, B, 0)
+    # integer data: many equal candidates; np.round gives -0 for small negatives
+    lp_i = np.round(log_pi).astype(np.float32)
+    A_i = np.round(logA * 2).astype(np.float32)
+    E_i = [np.round(e).astype(np.float32) for e in E_list]
+    m2, hmm2 = make_model(fv, lp_i, A_i)
+    run_beam(fv, m2, hmm2, E_i, B, 0)
+
+
+def test_dense_beam_cluster_engine_many_sequences(fv):
+    """More sequences than resident clusters: each cluster decodes several
+    sequences in turn (one long sequence among short ones, so that the
+    launch takes the cluster kernel)."""
+    rng = np.random.default_rng(77)
+    K = 512
+    log_pi, logA = W.random_model(K, rng)
+    m, hmm = make_model(fv, log_pi, logA)
+    lengths = [200] + list(rng.integers(1, 60, 44))
+    E_list = [W.gaussian_emissions(int(t), K, rng) for t in lengths]
+    run_beam(fv, m, hmm, E_list, 32, 0)
+
+
+def test_dense_beam_cluster_engine_discrete(fv):
+    """Symbol emissions (logB rows selected by the observations) on the
+    cluster engine."""
+    rng = np.random.default_rng(78)
+    K, V = 1024, 40
+    log_pi, logA = W.random_model(K, rng)
+    logB = np.log(rng.dirichlet(np.full(V, 0.5), K)).astype(np.float32)
+    m = fv.Model(log_pi, logA, logB=logB)
+    lengths = [1, 5, 90, 200]
+    obs = [rng.integers(0, V, t).astype(np.int32) for t in lengths]
+    b = fv.Batch(lengths, obs=torch.from_numpy(np.concatenate(obs)).cuda(), models=[m])
+    paths, scores = fv.decode([m], b, mode="beam", P=0, B=128)
+    paths, scores = paths.cpu().numpy(), scores.cpu().numpy()
+    hmm = oracle.HMM(log_pi, logA)
+    off = 0
+    for i, (t, o) in enumerate(zip(lengths, obs)):
+        p, s, st = oracle.beam(hmm, oracle.expand_discrete(logB, o), 128)
+        assert st == 0
+        assert np.array_equal(paths[off:off + t], p), f"seq {i}"
+        assert bits(scores[i]) == bits(s)
+        off += t
+
+
+def test_dense_beam_cluster_engine_infeasible(fv):
+    """A beam that empties (every candidate -inf) is reported as
+    FV_EINFEASIBLE, as the oracle finds it, and the next call decodes."""
+    rng = np.random.default_rng(79)
+    K = 512
+    log_pi, logA = W.random_model(K, rng)
+    # state 0 is the only possible start and leads nowhere
+    log_pi = np.full(K, -np.inf, np.float32)
+    log_pi[0] = 0.0
+    logA[0, :] = -np.inf
+    m, hmm = make_model(fv, log_pi, logA)
+    E = W.gaussian_emissions(10, K, rng)
+    assert oracle.beam(hmm, E, 16)[2] == 6
+    b = fv.Batch([10], E=torch.from_numpy(E).cuda(), models=[m])
+    with pytest.raises(fv._lib.FVError) as ei:
+        fv.decode([m], b, mode="beam", P=0, B=16)
+    assert ei.value.status == fv._lib.FV_EINFEASIBLE
+    log_pi2, logA2 = W.random_model(K, rng)
+    m2, hmm2 = make_model(fv, log_pi2, logA2)
+    run_beam(fv, m2, hmm2, [W.gaussian_emissions(30, K, rng)], 16, 0)
+
+
+def test_dense_beam_many_short_sequences_one_cta_each(fv):
+    """Many sequences of equal length finish sooner with one CTA each than
+    with one cluster each (the launch picks by the two makespans): the
+    single-CTA kernel's four-targets-per-thread path at K >= 512, P = 0,
+    against the oracle."""
+    rng = np.random.default_rng(80)
+    K = 512
+    log_pi, logA = _masked_model(K, rng, 0.2)
+    m, hmm = make_model(fv, log_pi, logA)
+    E_list = [W.gaussian_emissions(30, K, rng) for _ in range(160)]
+    run_beam(fv, m, hmm, E_list, 64, 0)
