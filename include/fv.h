@@ -85,6 +85,13 @@ typedef enum { FV_EMIT_DENSE = 0, FV_EMIT_DISCRETE = 1 } fv_emit_kind;
  * the per-step candidate storage differ (K entries instead of the states
  * the beam reaches).  A comparator for benchmarks. */
 #define FV_STATIC_BEAM 0x10u
+/* The call shares the GPU with other decodes running at the same time (a
+ * serving loop): take the kernel configuration with the least SM time per
+ * step rather than the one that finishes this call soonest on an idle GPU.
+ * Today this keeps dense beams (P = 0) on one CTA per sequence, which takes
+ * about a third of the SM time per step of one 8-CTA cluster per sequence.
+ * Results are the same either way. */
+#define FV_SHARED_GPU 0x20u
 /* Test hook for failure detection: the first CTA of the whole-GPU engine
  * (dense K > 1024) never publishes its step count, and CTA 1 of every 4- or
  * 8-CTA cluster of the streamed engine (256 < K <= 1024) withholds its

@@ -25,6 +25,7 @@ FV_NO_SORT = 0x2
 FV_CHECKED = 0x4
 FV_NO_TUNE = 0x8
 FV_STATIC_BEAM = 0x10
+FV_SHARED_GPU = 0x20
 FV_TEST_WITHHOLD_STEP = 0x80000000
 
 P = ctypes.c_void_p

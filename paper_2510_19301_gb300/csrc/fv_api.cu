@@ -465,6 +465,7 @@ fv_status decode_beam(const fv_model* models, int32_t n_models, const fv_batch* 
     ba.P = p->P;
     ba.complete = (p->flags & FV_COMPLETE_PRUNING) ? 1 : 0;
     ba.static_beam = (p->flags & FV_STATIC_BEAM) ? 1 : 0;
+    ba.per_cta = (p->flags & FV_SHARED_GPU) ? 1 : 0;
     ba.max_ctas = L.max_ctas;
     ba.scratch = ws + L.bscratch;
     ba.scratch_stride = L.bstride;

@@ -1565,10 +1565,12 @@ static int launch_beam_cluster(const BeamArgs& a, int max_jobs, cudaStream_t st,
 // cluster kernel when max(T_max, sum T / clusters) < r max(T_max, sum T / SMs),
 // the two makespans in units of the cluster's step time (sequences are
 // taken longest first).  Without the lengths: when every sequence gets its
-// own cluster.
+// own cluster.  Never under FV_SHARED_GPU: a cluster step takes about 2.5
+// times the SM time of a one-CTA step, which other decodes sharing the GPU
+// would pay for (measured in the serving loop: p50 519 -> 749 ms).
 static int launch_beam_dense_cluster(const BeamArgs& a, int max_jobs, cudaStream_t st, cudaError_t* err) {
   *err = cudaSuccess;
-  if (a.trans != FV_TRANS_DENSE || a.kind != kJobBeam || a.static_beam) return 1;
+  if (a.trans != FV_TRANS_DENSE || a.kind != kJobBeam || a.static_beam || a.per_cta) return 1;
   if (a.K < 512 || a.K > kDCMaxK || (a.K % 32) != 0 || ((uintptr_t)a.logA & 15u) != 0) return 1;
   const int W = a.Wcap < a.Bcap ? a.Wcap : a.Bcap;
   if (W < 1) return 1;

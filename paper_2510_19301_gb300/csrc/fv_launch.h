@@ -191,6 +191,7 @@ struct BeamArgs {
   // used only to choose between one CTA and one cluster per sequence
   int64_t sum_T;
   int32_t max_T;
+  int32_t per_cta;            // one CTA per sequence (FV_SHARED_GPU)
   WsHeader* hdr;
 };
 

@@ -219,8 +219,10 @@ class GpuBackend:
         import torch
 
         from . import Batch, Decoder, Model
+        from ._lib import FV_SHARED_GPU
         self.torch = torch
         self.Batch, self.Decoder, self.Model = Batch, Decoder, Model
+        self.FV_SHARED_GPU = FV_SHARED_GPU
         self.device = device
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
         self.free = list(range(n_streams))
@@ -321,8 +323,9 @@ class GpuBackend:
             models = [self.Model(*self._dirichlet_model(K, r.seed), device=self.device) for r in reqs]
             mi = list(range(len(reqs)))
         b = self.Batch(lengths, E=E, models=models, model_index=mi, device=self.device)
+        # launches overlap on the device: kernels with the least SM time per step
         dec = self.Decoder(models, b, mode=self._mode(r0), P=r0.P if r0.mode != "exact" else 1,
-                           B=r0.B if r0.mode == "beam" else 0)
+                           B=r0.B if r0.mode == "beam" else 0, flags=self.FV_SHARED_GPU)
         return dec, E, models
 
     def launch_batch(self, reqs):

@@ -238,3 +238,21 @@ def test_dense_beam_many_short_sequences_one_cta_each(fv):
     m, hmm = make_model(fv, log_pi, logA)
     E_list = [W.gaussian_emissions(30, K, rng) for _ in range(160)]
     run_beam(fv, m, hmm, E_list, 64, 0)
+
+
+def test_shared_gpu_flag_keeps_results(fv):
+    """FV_SHARED_GPU (one CTA per sequence for dense beams, as a serving loop
+    asks) decodes a lone K=1024 sequence exactly like the cluster kernel the
+    launch takes without it, and both equal the oracle."""
+    rng = np.random.default_rng(81)
+    K, B = 1024, 256
+    log_pi, logA = W.random_model(K, rng)
+    m, hmm = make_model(fv, log_pi, logA)
+    E = W.gaussian_emissions(150, K, rng)
+    b = fv.Batch([150], E=torch.from_numpy(E).cuda(), models=[m])
+    pc, sc = [x.clone() for x in fv.decode([m], b, mode="beam", P=0, B=B)]
+    ps, ss = fv.decode([m], b, mode="beam", P=0, B=B, flags=fv._lib.FV_SHARED_GPU)
+    assert torch.equal(pc, ps)
+    assert torch.equal(sc.view(torch.int32), ss.view(torch.int32))
+    p, s, st = oracle.beam(hmm, E, B)
+    assert st == 0 and np.array_equal(ps.cpu().numpy(), p) and bits(ss.cpu().numpy()[0]) == bits(s)
