@@ -24,6 +24,19 @@ def test_exports_every_declared_function(lib):
         assert hasattr(lib, n), f"libfv.so does not export {n}"
 
 
+def test_header_constants_match_binding():
+    """Every flag, status and enum value include/fv.h defines has the same
+    value in the Python binding."""
+    import re
+    src = open(L.HEADER).read()
+    defines = dict(re.findall(r"#define\s+(FV_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+|\d+)u?\b", src))
+    assert "FV_SHARED_GPU" in defines and "FV_STATIC_BEAM" in defines
+    for name, v in defines.items():
+        assert getattr(L, name) == int(v, 0), name
+    for name, v in re.findall(r"\b(FV_[A-Z0-9_]+)\s*=\s*(\d+)", src):
+        assert getattr(L, name) == int(v), name
+
+
 def test_status_strings(lib):
     for s in range(7):
         assert lib.fv_status_str(s)
