@@ -5,7 +5,9 @@
 // job from a global counter.  Beams of at least 64 states on large CSR state
 // spaces (P = 0) instead spread each sequence over a cluster of CTAs
 // (beam_csr_cluster_kernel, below), and so do dense beams with
-// 512 <= K <= 8192 (P = 0; beam_dense_cluster_kernel).  A beam
+// 512 <= K <= 8192 (P = 0; beam_dense_cluster_kernel).  Dense beams with
+// K <= 128 (P = 0) run small_beam_kernel, one CTA of a thread per state
+// holding its transition column in registers.  A beam
 // is the top-B finite candidates under (score desc, state id asc); it is
 // kept sorted by state id so that the next step visits its sources in
 // ascending order.  Per step:
@@ -1469,6 +1471,189 @@ __global__ void __launch_bounds__(kDCThreads, 1) beam_dense_cluster_kernel(BeamA
   }
 }
 
+// ---------------------------------------------------------------------------
+// Dynamic beam on small dense state spaces (K <= 128, P = 0): one CTA of KM
+// threads per sequence, thread j owning target j with the column logA[:, j]
+// in registers, as in the small-K exact engine.  delta_{t-1} is kept for all
+// K states, -inf outside the beam, so the max-plus over every row gives each
+// target its best beam source: rows outside the beam only add -inf, and the
+// lowest row reaching the maximum is the lowest beam slot, because the beam
+// is kept in id order.  That row's slot is the number of beam states below
+// it.  The top-B select ranks the finite candidates under (score desc, id
+// asc) inside the CTA, and warp ballots give each winner its position in id
+// order.  Same candidates, tie rules and beams as beam_kernel; a step costs
+// two block barriers instead of the general kernel's dozen.
+constexpr int kSBAhead = 4;               // emission scores loaded this many steps ahead
+constexpr int kSBLogB = 48 * 1024;        // bytes of a discrete table staged in shared memory at most
+
+template <int KM>
+__host__ __device__ inline bool sb_stage_logB(const BeamArgs& a) {
+  return a.emit != FV_EMIT_DENSE && (size_t)a.V * KM * sizeof(float) <= (size_t)kSBLogB;
+}
+
+template <int KM>
+__global__ void __launch_bounds__(KM) small_beam_kernel(BeamArgs a) {
+  constexpr int NWP = KM / 32;  // warps
+  constexpr int Q = KM / 4;     // rows per argmax chain
+  __shared__ __align__(16) float sd[2][KM];      // delta of the beam states, -inf elsewhere
+  __shared__ __align__(16) uint32_t skey[KM];    // this step's ordered candidate keys (0: not finite)
+  __shared__ uint32_t sbm[2][NWP];               // beam membership, one bit per state
+  extern __shared__ float sbB[];                 // discrete table as [symbol][state] (when it fits)
+  __shared__ int s_go;
+  if ((int)blockIdx.x >= a.order_count) return;
+  // an earlier kernel may have recorded an error: one thread reads the
+  // status word, so that the whole CTA takes the same decision
+  if (threadIdx.x == 0) s_go = a.hdr->status == 0;
+  __syncthreads();
+  if (!s_go) return;
+  const int K = a.K, j = threadIdx.x, lane = j & 31, w = j >> 5;
+  const bool own = j < K;
+  const int b = a.order[a.order_begin + blockIdx.x];
+  const Job jb = a.jobs[b];
+  const int T = jb.T;
+  const int W = a.Wcap < a.Bcap ? a.Wcap : a.Bcap;
+  float A[KM];
+#pragma unroll
+  for (int i = 0; i < KM; ++i) A[i] = (own && i < K) ? __ldg(a.logA + (int64_t)i * K + j) : -CUDART_INF_F;
+  const bool staged = sb_stage_logB<KM>(a);
+  if (staged) {
+    for (int x = 0; x < a.V; ++x) sbB[x * KM + j] = own ? __ldg(a.logB + (int64_t)j * a.V + x) : 0.f;
+    __syncthreads();
+  }
+  auto emit = [&](int t) -> float {
+    if (a.emit == FV_EMIT_DENSE) return __ldg(a.E + jb.e_off + (int64_t)t * K + j);
+    const int x = __ldg(a.obs + jb.e_off + t);
+    return staged ? sbB[x * KM + j] : __ldg(a.logB + (int64_t)j * a.V + x);
+  };
+  float er[kSBAhead];  // E_t .. E_{t+kSBAhead-1} of this state, oldest first
+#pragma unroll
+  for (int k = 0; k < kSBAhead; ++k) er[k] = (own && k < T) ? emit(k) : 0.f;
+  int cur = 0;
+  for (int t = 0; t < T; ++t) {
+    const float e = er[0];
+#pragma unroll
+    for (int k = 0; k + 1 < kSBAhead; ++k) er[k] = er[k + 1];
+    er[kSBAhead - 1] = (own && t + kSBAhead < T) ? emit(t + kSBAhead) : 0.f;
+    float c;
+    int src = 0;
+    if (t == 0) {
+      c = own ? __fadd_rn(__ldg(a.log_pi + j), e) : -CUDART_INF_F;
+    } else {
+      // candidates in ascending row order in four interleaved chains over
+      // quarters of the rows; the first strictly larger one is kept, and the
+      // chains merge in row order
+      const float4* dv = reinterpret_cast<const float4*>(sd[cur]);
+      float bq[4];
+      int gq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bq[q] = -CUDART_INF_F;
+        gq[q] = q * Q;
+      }
+#pragma unroll
+      for (int i4 = 0; i4 < Q / 4; ++i4)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = q * Q + 4 * i4;
+          const float4 x = dv[i / 4];
+          float y = __fadd_rn(x.x, A[i]);
+          if (y > bq[q]) { bq[q] = y; gq[q] = i; }
+          y = __fadd_rn(x.y, A[i + 1]);
+          if (y > bq[q]) { bq[q] = y; gq[q] = i + 1; }
+          y = __fadd_rn(x.z, A[i + 2]);
+          if (y > bq[q]) { bq[q] = y; gq[q] = i + 2; }
+          y = __fadd_rn(x.w, A[i + 3]);
+          if (y > bq[q]) { bq[q] = y; gq[q] = i + 3; }
+        }
+      float bv = bq[0];
+      int g = gq[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (bq[q] > bv) { bv = bq[q]; g = gq[q]; }
+      c = own ? __fadd_rn(bv, e) : -CUDART_INF_F;
+      // the source's slot: beam states with a lower id
+#pragma unroll
+      for (int q = 0; q < NWP; ++q) {
+        const uint32_t m = sbm[cur][q];
+        if (32 * q + 32 <= g) src += __popc(m);
+        else if (32 * q < g) src += __popc(m & ((1u << (g - 32 * q)) - 1u));
+      }
+    }
+    // ---- top-W of the finite candidates under (score desc, id asc)
+    const uint32_t key = isfinite(c) ? ord_key(c) : 0u;
+    skey[j] = key;
+    const int nfin = __syncthreads_count(key != 0u);
+    bool take = key != 0u;
+    if (take && nfin > W) {
+      int rank = 0;  // finite candidates ahead of this one (key 0 never is)
+      const uint4* kv = reinterpret_cast<const uint4*>(skey);
+#pragma unroll 8
+      for (int i4 = 0; i4 < KM / 4; ++i4) {
+        const uint4 u = kv[i4];
+        const int i = 4 * i4;
+        rank += (u.x > key || (u.x == key && i < j)) ? 1 : 0;
+        rank += (u.y > key || (u.y == key && i + 1 < j)) ? 1 : 0;
+        rank += (u.z > key || (u.z == key && i + 2 < j)) ? 1 : 0;
+        rank += (u.w > key || (u.w == key && i + 3 < j)) ? 1 : 0;
+      }
+      take = rank < W;
+    }
+    sd[cur ^ 1][j] = take ? c : -CUDART_INF_F;
+    const uint32_t bal = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) sbm[cur ^ 1][w] = bal;
+    __syncthreads();  // the next beam (values and membership) is complete
+    int nb = 0, pos = __popc(bal & ((1u << lane) - 1u));
+#pragma unroll
+    for (int q = 0; q < NWP; ++q) {
+      const int cnt = __popc(sbm[cur ^ 1][q]);
+      nb += cnt;
+      if (q < w) pos += cnt;
+    }
+    if (nb == 0) {  // the beam emptied (the same in every thread)
+      if (j == 0) set_status(a.hdr, FV_EINFEASIBLE, (uint32_t)b);
+      return;
+    }
+    if (take) {
+      a.bp_id[jb.aux_off + (int64_t)t * a.Wcap + pos] = j;
+      a.bp_src[jb.aux_off + (int64_t)t * a.Wcap + pos] = src;
+    }
+    cur ^= 1;
+  }
+  if (j < 32) {
+    // best final entry: highest score, lowest id (states outside the beam are -inf)
+    float v = sd[cur][lane];
+    int qi = lane;
+#pragma unroll
+    for (int k = 1; k < NWP; ++k) {
+      const float vk = sd[cur][lane + 32 * k];
+      if (vk > v) { v = vk; qi = lane + 32 * k; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oq = __shfl_xor_sync(0xffffffffu, qi, o);
+      if (ov > v || (ov == v && oq < qi)) { v = ov; qi = oq; }
+    }
+    if (lane == 0) {
+      int slot = 0;
+      for (int q = 0; q < NWP; ++q) {
+        const uint32_t m = sbm[cur][q];
+        if (32 * q + 32 <= qi) slot += __popc(m);
+        else if (32 * q < qi) slot += __popc(m & ((1u << (qi - 32 * q)) - 1u));
+      }
+      a.scores[b] = sd[cur][qi];
+      a.qlast[b] = slot;
+    }
+  }
+}
+
+template <int KM>
+static cudaError_t launch_small_beam_cfg(const BeamArgs& a, int jobs, cudaStream_t st) {
+  const size_t sm = sb_stage_logB<KM>(a) ? (size_t)a.V * KM * sizeof(float) : 0;
+  small_beam_kernel<KM><<<jobs, KM, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 // Backtrack through per-step beam backpointers (one thread per sequence).
 __global__ void beam_backtrack_kernel(const Job* jobs, const int32_t* order, int32_t begin, int32_t count,
                                       int32_t Wcap, const int32_t* bp_id, const int32_t* bp_src,
@@ -1619,6 +1804,10 @@ cudaError_t launch_beam(const BeamArgs& a, int max_jobs, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (a.trans == FV_TRANS_DENSE && a.kind == kJobBeam && !a.static_beam && a.K <= 128) {
+    if (max_jobs < 1) return cudaSuccess;
+    return a.K <= 64 ? launch_small_beam_cfg<64>(a, max_jobs, st) : launch_small_beam_cfg<128>(a, max_jobs, st);
+  }
   {
     cudaError_t ce;
     if (launch_beam_cluster(a, max_jobs, st, &ce) == 0) return ce;

@@ -256,3 +256,66 @@ def test_shared_gpu_flag_keeps_results(fv):
     assert torch.equal(sc.view(torch.int32), ss.view(torch.int32))
     p, s, st = oracle.beam(hmm, E, B)
     assert st == 0 and np.array_equal(ps.cpu().numpy(), p) and bits(ss.cpu().numpy()[0]) == bits(s)
+
+
+@pytest.mark.parametrize("K", [1, 5, 33, 64, 65, 100, 128])
+def test_small_k_beam_engine(fv, K):
+    """Dense beams with K <= 128 (P = 0) run one CTA per sequence with a
+    thread per state (delta -inf outside the beam, full max-plus, rank
+    select): same paths and scores as the oracle for narrow and full-width
+    beams, with absent transitions, integer data (equal candidates, signed
+    zeros) and many sequences."""
+    rng = np.random.default_rng(300 + K)
+    log_pi, logA = _masked_model(K, rng, 0.3)
+    m, hmm = make_model(fv, log_pi, logA)
+    lengths = [1, 2, 3, 40, 300] + list(rng.integers(1, 80, 40))
+    E_list = [W.gaussian_emissions(int(t), K, rng) for t in lengths]
+    lp_i = np.round(log_pi).astype(np.float32)
+    A_i = np.round(logA * 2).astype(np.float32)
+    E_i = [np.round(e).astype(np.float32) for e in E_list]
+    m2, hmm2 = make_model(fv, lp_i, A_i)
+    for B in sorted({1, 3, 16, max(1, K - 1), K, K + 5}):
+        run_beam(fv, m, hmm, E_list, B, 0)
+        run_beam(fv, m2, hmm2, E_i, B, 0)
+
+
+@pytest.mark.parametrize("K,V", [(64, 32), (128, 200)])
+def test_small_k_beam_engine_discrete(fv, K, V):
+    """Symbol emissions on the small-K beam engine: the table staged in
+    shared memory (64 x 32) and read from global memory (128 x 200)."""
+    rng = np.random.default_rng(K + V)
+    log_pi, logA = W.random_model(K, rng)
+    logB = np.log(rng.dirichlet(np.full(V, 0.5), K)).astype(np.float32)
+    m = fv.Model(log_pi, logA, logB=logB)
+    lengths = [1, 7, 300, 1000]
+    obs = [rng.integers(0, V, t).astype(np.int32) for t in lengths]
+    b = fv.Batch(lengths, obs=torch.from_numpy(np.concatenate(obs)).cuda(), models=[m])
+    hmm = oracle.HMM(log_pi, logA)
+    for B in (1, 16, K):
+        paths, scores = fv.decode([m], b, mode="beam", P=0, B=B)
+        paths, scores = paths.cpu().numpy(), scores.cpu().numpy()
+        off = 0
+        for i, (t, o) in enumerate(zip(lengths, obs)):
+            p, s, st = oracle.beam(hmm, oracle.expand_discrete(logB, o), B)
+            assert st == 0
+            assert np.array_equal(paths[off:off + t], p), f"seq {i} B={B}"
+            assert bits(scores[i]) == bits(s)
+            off += t
+
+
+def test_small_k_beam_engine_infeasible(fv):
+    """An emptied beam on the small-K engine is FV_EINFEASIBLE, as in the
+    oracle."""
+    rng = np.random.default_rng(82)
+    K = 64
+    log_pi, logA = W.random_model(K, rng)
+    log_pi = np.full(K, -np.inf, np.float32)
+    log_pi[3] = 0.0
+    logA[3, :] = -np.inf
+    m, hmm = make_model(fv, log_pi, logA)
+    E = W.gaussian_emissions(10, K, rng)
+    assert oracle.beam(hmm, E, 4)[2] == 6
+    b = fv.Batch([10], E=torch.from_numpy(E).cuda(), models=[m])
+    with pytest.raises(fv._lib.FVError) as ei:
+        fv.decode([m], b, mode="beam", P=0, B=4)
+    assert ei.value.status == fv._lib.FV_EINFEASIBLE
